@@ -1,0 +1,149 @@
+/*
+ * gsofa.h - C ABI of the GB300 symbolic LU library (gSoFa, arXiv 2007.00840).
+ *
+ * The library computes the static symbolic LU factorisation of a square
+ * nonsymmetric sparsity pattern A (no pivoting, nonzero pivots):
+ *
+ *   - the L and U patterns of L+U (Theorem 1, Section 2.1: entry (i, j) is
+ *     nonzero iff A(i, j) != 0, i == j, or G(A) has a path i -> j whose
+ *     intermediate vertices are all numbered below min(i, j));
+ *   - the number of fill-ins of every row;
+ *   - the T3 supernode partition (Definition 1, Section 2.2), limited to
+ *     aligned chunks of `chunk_size` rows (Section 5, Eq. 1).
+ *
+ * The fill pattern is found by the multi-source maxId traversal of Section 4
+ * (Fig. 5): many source rows are traversed concurrently, every frontier vertex
+ * of every source is expanded in parallel, and a vertex is revisited whenever
+ * its maxId (the smallest largest-intermediate over the paths found so far)
+ * drops.  Supernodes use the two-phase detection of Section 5 (Fig. 7).
+ *
+ * Conventions shared by every entry point
+ *   - Input: CSR with int32 row pointers (n+1, rowptr[0] == 0, non-decreasing)
+ *     and int32 column indices (rowptr[n] entries, 0 <= col < n, strictly
+ *     increasing inside each row).  Inputs are borrowed and never modified.
+ *     The diagonal may be absent; U(i,i) is emitted regardless.
+ *   - Output: L holds the strictly lower part (unit diagonal implied, not
+ *     stored); U holds the upper part including the diagonal.  Column indices
+ *     are sorted ascending inside every row.  Row pointers are int64.
+ *   - Errors: every function returns GSOFA_OK (0) or a negative GSOFA_E_*
+ *     code; on error the result struct is left zeroed and nothing needs to be
+ *     freed.  gsofa_strerror() names a code.
+ *   - Threads: calls on different streams may run concurrently from different
+ *     host threads; one result must not be used from two threads at once.
+ */
+#ifndef GSOFA_H
+#define GSOFA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSOFA_OK             0
+#define GSOFA_E_INVAL       -1  /* bad argument or malformed CSR (see gsofa_result.err_detail) */
+#define GSOFA_E_NOMEM       -2  /* device or host allocation failed / budget too small */
+#define GSOFA_E_CUDA        -3  /* a CUDA runtime call failed */
+#define GSOFA_E_NOCONVERGE  -4  /* a traversal hit its iteration cap (never expected) */
+#define GSOFA_E_TIMEOUT     -5  /* a bounded host-side wait ran out */
+#define GSOFA_E_BUSY        -6  /* server admission queue is full */
+#define GSOFA_E_NOTFOUND    -7  /* unknown ticket */
+#define GSOFA_E_PENDING     -8  /* request not finished yet (gsofa_server_poll) */
+
+/* Tuning knobs.  Zero in any field selects the default. */
+typedef struct gsofa_options {
+    int32_t chunk_size;          /* rows per supernode chunk = maximum supernode size (default 128, Section 5) */
+    int32_t threads_per_source;  /* CTA size of the traversal kernels (default 512; 128..1024, multiple of 32) */
+    int32_t smem_max_source;     /* sources below this use shared-memory labels (default 0: as many as fit;
+                                    -1: none, every source uses the global-memory tier) */
+    int32_t max_concurrent;      /* global-label tier: concurrent source slots (default: one per SM) */
+    int64_t mem_budget_bytes;    /* cap on library working memory per call (default: none) */
+    int32_t fill_first;          /* 1: skip lowering the maxId of a vertex already known to be a fill
+                                    (the optional "line 9.5" of Section 4); same result */
+    int32_t collect_stats;       /* 1: record per-phase CUDA-event times and work counters */
+    int32_t validate;            /* 0 or 1: check the CSR on the device first (default 1); 2: skip */
+    int32_t reserved[7];
+} gsofa_options;
+
+/* Per-call statistics (filled when options.collect_stats == 1). */
+typedef struct gsofa_stats {
+    float ms_validate, ms_traverse, ms_emit, ms_supernode, ms_total;
+    float ms_traverse_smem, ms_traverse_global;
+    int32_t traverse_launches;
+    int32_t kernel_launches;     /* every kernel this call launched */
+    int64_t vertices_expanded;   /* frontier expansions, revisits included */
+    int64_t edges_scanned;       /* adjacency entries read by expansions */
+    int64_t pool_retries;        /* times the row pool had to grow and the traversal rerun */
+} gsofa_stats;
+
+/* Result.  Arrays are owned by the library and released by gsofa_free().
+ * on_device == 1: arrays are device pointers (same device as the call);
+ * on_device == 0: host pointers. */
+typedef struct gsofa_result {
+    int32_t n;
+    int32_t n_super;             /* number of supernodes */
+    int64_t nnz_L, nnz_U;        /* U counts the diagonal */
+    int64_t *L_rowptr;           /* n+1 */
+    int32_t *L_colidx;           /* nnz_L */
+    int64_t *U_rowptr;           /* n+1 */
+    int32_t *U_colidx;           /* nnz_U */
+    int32_t *fill_count;         /* n: entries of row i of L+U not in A (diagonal counted as present) */
+    int32_t *super_start;        /* n_super+1: first row of each supernode, then n */
+    int32_t on_device;
+    int32_t err_detail;          /* for GSOFA_E_INVAL: first offending row (or -1) */
+    gsofa_stats stats;
+    void *_priv;                 /* library bookkeeping */
+} gsofa_result;
+
+/* Fill *opt with the defaults. */
+int gsofa_default_options(gsofa_options *opt);
+
+/*
+ * gsofa_symbolic - host CSR in, host result out (Sections 4 and 5).
+ *   n        order of A (n >= 0)
+ *   rowptr   host int32[n+1]; colidx host int32[rowptr[n]]
+ *   opt      NULL for defaults
+ *   out      zeroed by the call, then filled; release with gsofa_free().
+ * Copies A to the current CUDA device, runs gsofa_symbolic_device on an
+ * internal stream, copies the result back and waits.  Blocking.
+ */
+int gsofa_symbolic(int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                   const gsofa_options *opt, gsofa_result *out);
+
+/*
+ * gsofa_symbolic_device - device CSR in, device result out.
+ *   d_rowptr, d_colidx  device pointers on the current device (borrowed)
+ *   stream              cudaStream_t (NULL = legacy default stream)
+ * All kernels run on `stream`.  The call reads back the output sizes once
+ * (a stream synchronisation) and returns after the result is complete.
+ */
+int gsofa_symbolic_device(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
+                          const gsofa_options *opt, void *stream, gsofa_result *out);
+
+/*
+ * gsofa_batch - many independent matrices in one pass (spec batching of
+ * the Section 4/5 method).  Matrix k is (n[k], d_rowptr[k], d_colidx[k]) on the
+ * device.  The sources of all matrices are scheduled together in persistent
+ * traversal kernels (largest source first); outs[k] receives matrix k's
+ * device result (release each with gsofa_free()).
+ */
+int gsofa_batch(int32_t count, const int32_t *n, const int32_t *const *d_rowptr,
+                const int32_t *const *d_colidx, const gsofa_options *opt, void *stream,
+                gsofa_result *outs);
+
+/* Release every array of *res (device or host) and zero it.  NULL-safe.
+ * Device arrays are freed stream-ordered on the stream of the call that made
+ * them; the caller must not use them afterwards. */
+void gsofa_free(gsofa_result *res);
+
+/* Human-readable name of an error code. */
+const char *gsofa_strerror(int code);
+
+/* Library version as an integer (major*10000 + minor*100 + patch). */
+int gsofa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSOFA_H */

@@ -1,0 +1,218 @@
+"""GB300 sparse symbolic LU factorisation (gSoFa, arXiv 2007.00840).
+
+Thin Python binding over ``libgsofa.so`` (C ABI: ``include/gsofa.h``).  Every
+step of the computation runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch is used for device memory and streams.
+
+    import paper_2007_00840_gb300 as gs
+    r = gs.symbolic_device(rowptr_cuda, colidx_cuda)      # torch int32 CUDA tensors
+    r.L_rowptr, r.L_colidx, r.U_rowptr, r.U_colidx, r.fill_count, r.super_start
+    h = gs.symbolic_host(rowptr_np, colidx_np)            # numpy in, numpy out
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import GsofaError, gsofa_options, gsofa_result
+
+__all__ = ["options", "symbolic_device", "symbolic_host", "batch_device", "DeviceResult", "HostResult",
+           "GsofaError", "load", "version"]
+
+load = _lib.load
+
+
+def version() -> int:
+    return load().gsofa_version()
+
+
+def options(**kw) -> gsofa_options:
+    """gsofa_options with defaults, overridden by keyword (field names of the C struct)."""
+    lib = load()
+    o = gsofa_options()
+    lib.gsofa_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class _CAI:
+    """__cuda_array_interface__ holder that keeps the owning result alive."""
+
+    def __init__(self, ptr: int, count: int, typestr: str, owner, stream: int):
+        self.__cuda_array_interface__ = {
+            "shape": (int(count),), "typestr": typestr, "data": (int(ptr) if count else 0, False),
+            "version": 3, "strides": None, "stream": stream if stream else None,
+        }
+        self._owner = owner
+
+
+class _Owner:
+    def __init__(self, res: gsofa_result):
+        self.res = res
+
+    def __del__(self):
+        try:
+            _lib.load().gsofa_free(ctypes.byref(self.res))
+        except Exception:
+            pass
+
+
+def _stats(res: gsofa_result) -> dict:
+    s = res.stats
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+class DeviceResult:
+    """Device-resident result; the tensors alias library memory (freed when all are gone)."""
+
+    def __init__(self, res: gsofa_result, stream: int):
+        import torch
+        own = _Owner(res)
+        n = res.n
+
+        def t(ptr, count, typestr, dtype):
+            if count == 0:
+                return torch.empty(0, dtype=dtype, device="cuda")
+            return torch.as_tensor(_CAI(ptr, count, typestr, own, stream), device="cuda")
+
+        self.n = n
+        self.nnz_L = int(res.nnz_L)
+        self.nnz_U = int(res.nnz_U)
+        self.n_super = int(res.n_super)
+        self.L_rowptr = t(res.L_rowptr, n + 1, "<i8", torch.int64)
+        self.L_colidx = t(res.L_colidx, res.nnz_L, "<i4", torch.int32)
+        self.U_rowptr = t(res.U_rowptr, n + 1, "<i8", torch.int64)
+        self.U_colidx = t(res.U_colidx, res.nnz_U, "<i4", torch.int32)
+        self.fill_count = t(res.fill_count, n, "<i4", torch.int32)
+        self.super_start = t(res.super_start, res.n_super + 1, "<i4", torch.int32)
+        self.stats = _stats(res)
+        self._owner = own
+
+    def to_host(self) -> "HostResult":
+        return HostResult(self.n, self.L_rowptr.cpu().numpy(), self.L_colidx.cpu().numpy(),
+                          self.U_rowptr.cpu().numpy(), self.U_colidx.cpu().numpy(),
+                          self.fill_count.cpu().numpy(), self.super_start.cpu().numpy(), self.stats)
+
+
+class HostResult:
+    def __init__(self, n, L_rowptr, L_colidx, U_rowptr, U_colidx, fill_count, super_start, stats=None):
+        self.n = n
+        self.L_rowptr, self.L_colidx = L_rowptr, L_colidx
+        self.U_rowptr, self.U_colidx = U_rowptr, U_colidx
+        self.fill_count, self.super_start = fill_count, super_start
+        self.nnz_L, self.nnz_U = int(L_rowptr[-1]), int(U_rowptr[-1])
+        self.n_super = int(super_start.size - 1)
+        self.stats = stats or {}
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def symbolic_device(rowptr, colidx, n: int | None = None, opts: gsofa_options | None = None,
+                    stream=None) -> DeviceResult:
+    """Symbolic LU of a device CSR (int32 CUDA tensors) -> DeviceResult (gsofa_symbolic_device)."""
+    import torch
+    lib = load()
+    if not (rowptr.is_cuda and colidx.is_cuda):
+        raise ValueError("symbolic_device needs CUDA tensors; use symbolic_host for host arrays")
+    if rowptr.dtype != torch.int32 or colidx.dtype != torch.int32:
+        raise TypeError("rowptr and colidx must be int32")
+    rowptr = rowptr.contiguous()
+    colidx = colidx.contiguous()
+    n = int(rowptr.numel() - 1) if n is None else int(n)
+    res = gsofa_result()
+    sh = _stream_handle(stream)
+    rc = lib.gsofa_symbolic_device(n, ctypes.c_void_p(rowptr.data_ptr()),
+                                   ctypes.c_void_p(colidx.data_ptr() if colidx.numel() else rowptr.data_ptr()),
+                                   ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(sh),
+                                   ctypes.byref(res))
+    if rc != 0:
+        raise GsofaError(rc, res.err_detail, "gsofa_symbolic_device")
+    return DeviceResult(res, sh)
+
+
+def symbolic_host_raw(rowptr: np.ndarray, colidx: np.ndarray, opts: gsofa_options | None = None) -> gsofa_result:
+    """gsofa_symbolic on host arrays; returns the raw result (caller frees with free_raw)."""
+    lib = load()
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    n = int(rowptr.size - 1)
+    res = gsofa_result()
+    ci = colidx if colidx.size else np.zeros(1, np.int32)
+    rc = lib.gsofa_symbolic(n, rowptr.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(res))
+    if rc != 0:
+        raise GsofaError(rc, res.err_detail, "gsofa_symbolic")
+    return res
+
+
+def free_raw(res: gsofa_result) -> None:
+    load().gsofa_free(ctypes.byref(res))
+
+
+def _host_array(ptr, count, ctype, dtype):
+    if count == 0:
+        return np.zeros(0, dtype=dtype)
+    buf = (ctype * int(count)).from_address(int(ptr))
+    return np.frombuffer(buf, dtype=dtype).copy()
+
+
+def symbolic_host(rowptr: np.ndarray, colidx: np.ndarray, opts: gsofa_options | None = None) -> HostResult:
+    """Symbolic LU of a host CSR (numpy int32) -> HostResult with numpy arrays (gsofa_symbolic)."""
+    res = symbolic_host_raw(rowptr, colidx, opts)
+    try:
+        n = res.n
+        out = HostResult(
+            n,
+            _host_array(res.L_rowptr, n + 1, ctypes.c_int64, np.int64),
+            _host_array(res.L_colidx, res.nnz_L, ctypes.c_int32, np.int32),
+            _host_array(res.U_rowptr, n + 1, ctypes.c_int64, np.int64),
+            _host_array(res.U_colidx, res.nnz_U, ctypes.c_int32, np.int32),
+            _host_array(res.fill_count, n, ctypes.c_int32, np.int32),
+            _host_array(res.super_start, res.n_super + 1, ctypes.c_int32, np.int32),
+            _stats(res),
+        )
+    finally:
+        free_raw(res)
+    return out
+
+
+def batch_device(mats, opts: gsofa_options | None = None, stream=None) -> list:
+    """Many device CSRs [(rowptr, colidx), ...] in one gsofa_batch call -> list of DeviceResult."""
+    lib = load()
+    k = len(mats)
+    ns = (ctypes.c_int32 * max(k, 1))()
+    rps = (ctypes.c_void_p * max(k, 1))()
+    cis = (ctypes.c_void_p * max(k, 1))()
+    keep = []
+    for i, (rp, ci) in enumerate(mats):
+        rp = rp.contiguous()
+        ci = ci.contiguous()
+        keep.append((rp, ci))
+        ns[i] = rp.numel() - 1
+        rps[i] = rp.data_ptr()
+        cis[i] = ci.data_ptr() if ci.numel() else rp.data_ptr()
+    outs = (gsofa_result * max(k, 1))()
+    sh = _stream_handle(stream)
+    rc = lib.gsofa_batch(k, ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(rps, ctypes.c_void_p),
+                         ctypes.cast(cis, ctypes.c_void_p), ctypes.byref(opts) if opts is not None else None,
+                         ctypes.c_void_p(sh), ctypes.cast(outs, ctypes.c_void_p))
+    if rc != 0:
+        raise GsofaError(rc, -1, "gsofa_batch")
+    res = []
+    for i in range(k):
+        r = gsofa_result()
+        ctypes.pointer(r)[0] = outs[i]
+        res.append(DeviceResult(r, sh))
+    return res

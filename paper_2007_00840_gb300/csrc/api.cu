@@ -1,0 +1,692 @@
+// Host side of libgsofa: argument checks, device memory, kernel sequencing
+// and the extern "C" entry points declared in include/gsofa.h.
+//
+// One call = validate the CSR (Section 2.4 input) -> maxId traversal of every
+// source row (Section 4; shared-memory tier for sources whose maxId array fits
+// on chip, global tier for the rest) -> T3 supernode flags (Section 5) ->
+// one read-back of the sizes -> prefix sums, row compaction into L/U CSR and
+// the supernode list.
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "gsofa.h"
+#include "internal.cuh"
+
+namespace gsofa {
+
+int trav_smem_static_bytes();                    // traverse_smem.cu
+int trav_smem_occupancy(int block, size_t dyn_bytes);  // traverse_smem.cu
+
+namespace {
+
+struct Ctx {
+  int device = 0;
+  int sms = 0;
+  int smem_optin = 0;
+  cudaMemPool_t mpool = nullptr;
+  // global-tier slots (persist across calls: the maxId windows live in them)
+  std::mutex gmu;
+  uint32_t* g_lab = nullptr;
+  int32_t* g_queue = nullptr;
+  uint32_t* g_inq = nullptr;
+  uint32_t* g_rowbits = nullptr;
+  uint32_t* g_base = nullptr;
+  int64_t g_cap = 0;
+  int g_slots = 0;
+  cudaEvent_t g_done = nullptr;
+  // row-pool size that fitted last time, by matrix order
+  std::mutex hmu;
+  std::map<int32_t, long long> pool_hint;
+};
+
+std::mutex g_ctx_mu;
+Ctx* g_ctx[128] = {nullptr};
+
+struct Priv {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  cudaMemPool_t mpool = nullptr;
+  void* host_block = nullptr;   // host results: one pinned block holding every array
+  size_t host_cap = 0;
+};
+
+// Pinned host blocks are expensive to create (page locking), so results of the
+// host entry point reuse them: gsofa_free returns a block here.
+struct PinnedCache {
+  std::mutex mu;
+  std::multimap<size_t, void*> blocks;
+  size_t cached = 0;
+  size_t limit = (size_t)8 << 30;
+};
+PinnedCache g_pinned;
+
+void* pinned_get(size_t bytes, size_t* cap) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned.mu);
+    auto it = g_pinned.blocks.lower_bound(bytes);
+    if (it != g_pinned.blocks.end() && it->first <= 2 * bytes + (1 << 20)) {
+      void* p = it->second;
+      *cap = it->first;
+      g_pinned.cached -= it->first;
+      g_pinned.blocks.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *cap = bytes;
+  return p;
+}
+
+void pinned_put(void* p, size_t cap) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_pinned.mu);
+    if (g_pinned.cached + cap <= g_pinned.limit) {
+      g_pinned.blocks.emplace(cap, p);
+      g_pinned.cached += cap;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
+double timeout_seconds() {
+  const char* e = std::getenv("GSOFA_TIMEOUT_S");
+  if (e) {
+    const double v = std::atof(e);
+    if (v > 0) return v;
+  }
+  return 600.0;
+}
+
+// Bounded wait for all work queued on `st` (never an unbounded block).
+int wait_stream(cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const double limit = timeout_seconds();
+  int spins = 0;
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return GSOFA_OK;
+    if (e != cudaErrorNotReady) return GSOFA_E_CUDA;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return GSOFA_E_TIMEOUT;
+    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+Ctx* get_ctx(int* err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    *err = GSOFA_E_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  if (g_ctx[dev]) return g_ctx[dev];
+  Ctx* c = new Ctx();
+  c->device = dev;
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    delete c;
+    *err = GSOFA_E_CUDA;
+    return nullptr;
+  }
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  if (cudaMemPoolCreate(&c->mpool, &props) != cudaSuccess) {
+    delete c;
+    *err = GSOFA_E_CUDA;
+    return nullptr;
+  }
+  uint64_t thr = UINT64_MAX;  // keep freed blocks for reuse by later calls
+  cudaMemPoolSetAttribute(c->mpool, cudaMemPoolAttrReleaseThreshold, &thr);
+  cudaEventCreateWithFlags(&c->g_done, cudaEventDisableTiming);
+  g_ctx[dev] = c;
+  return c;
+}
+
+template <typename T>
+cudaError_t palloc(Ctx* c, T** p, size_t count, cudaStream_t st) {
+  *p = nullptr;
+  const size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+  return cudaMallocFromPoolAsync((void**)p, bytes, c->mpool, st);
+}
+
+template <typename T>
+void pfree(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+
+// Make sure the global-tier slots hold `slots` x `cap` vertices.  Caller holds gmu.
+int ensure_slots(Ctx* c, int64_t cap, int slots, cudaStream_t st) {
+  if (c->g_lab && c->g_cap >= cap && c->g_slots >= slots) return GSOFA_OK;
+  // the previous user of the slots must be done before they are replaced
+  cudaEventSynchronize(c->g_done);
+  cudaFree(c->g_lab);
+  cudaFree(c->g_queue);
+  cudaFree(c->g_inq);
+  cudaFree(c->g_rowbits);
+  cudaFree(c->g_base);
+  c->g_lab = nullptr; c->g_queue = nullptr; c->g_inq = nullptr; c->g_rowbits = nullptr; c->g_base = nullptr;
+  c->g_cap = 0; c->g_slots = 0;
+  const int64_t capW = (cap + 31) / 32;
+  if (cudaMalloc(&c->g_lab, sizeof(uint32_t) * cap * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_queue, sizeof(int32_t) * 2 * cap * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_inq, sizeof(uint32_t) * capW * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_rowbits, sizeof(uint32_t) * capW * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_base, sizeof(uint32_t) * slots) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->g_lab); cudaFree(c->g_queue); cudaFree(c->g_inq); cudaFree(c->g_rowbits); cudaFree(c->g_base);
+    c->g_lab = nullptr; c->g_queue = nullptr; c->g_inq = nullptr; c->g_rowbits = nullptr; c->g_base = nullptr;
+    return GSOFA_E_NOMEM;
+  }
+  cudaMemsetAsync(c->g_lab, 0xFF, sizeof(uint32_t) * cap * slots, st);
+  cudaMemsetAsync(c->g_inq, 0, sizeof(uint32_t) * capW * slots, st);
+  cudaMemsetAsync(c->g_rowbits, 0, sizeof(uint32_t) * capW * slots, st);
+  cudaMemsetAsync(c->g_base, 0xFF, sizeof(uint32_t) * slots, st);
+  c->g_cap = cap;
+  c->g_slots = slots;
+  return cudaGetLastError() == cudaSuccess ? GSOFA_OK : GSOFA_E_CUDA;
+}
+
+DevCounters* pinned_counters() {
+  thread_local DevCounters* h = nullptr;
+  if (!h) {
+    if (cudaMallocHost(&h, sizeof(DevCounters)) != cudaSuccess) h = nullptr;
+  }
+  return h;
+}
+
+struct Events {
+  bool on = false;
+  cudaEvent_t e[8] = {nullptr};
+  void create(bool enable) {
+    on = enable;
+    if (!on) return;
+    for (auto& x : e) cudaEventCreate(&x);
+  }
+  void rec(int i, cudaStream_t st) {
+    if (on) cudaEventRecord(e[i], st);
+  }
+  float ms(int a, int b) {
+    float v = 0.f;
+    if (on) cudaEventElapsedTime(&v, e[a], e[b]);
+    return v;
+  }
+  ~Events() {
+    if (on)
+      for (auto& x : e) cudaEventDestroy(x);
+  }
+};
+
+void zero_result(gsofa_result* out) { std::memset(out, 0, sizeof(*out)); }
+
+struct Plan {
+  int32_t S = 0;          // shared tier: sources [0, S)
+  int smem_block = 512;
+  int smem_grid = 0;
+  int glob_block = 512;
+  int glob_grid = 0;
+};
+
+int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
+  const int stat = trav_smem_static_bytes();
+  const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
+  int32_t S = trav_smem_max_S(n, limit);
+  if (o.smem_max_source > 0 && o.smem_max_source < S) S = o.smem_max_source;
+  if (o.smem_max_source < 0) S = 0;  // every source in the global tier
+  if (S > n) S = n;
+  if (S < 0) S = 0;
+  p->S = S;
+  if (S > 0) {
+    const size_t bytes = trav_smem_bytes(n, S);
+    int block = o.threads_per_source;
+    if (block <= 0) block = bytes > (size_t)c->smem_optin / 2 ? 1024 : 512;
+    p->smem_block = block;
+    int occ = trav_smem_occupancy(block, bytes);
+    if (occ < 1) return GSOFA_E_CUDA;
+    p->smem_grid = c->sms * occ;
+  }
+  if (S < n) {
+    int block = o.threads_per_source > 0 ? o.threads_per_source : 512;
+    p->glob_block = block;
+    int slots = o.max_concurrent > 0 ? o.max_concurrent : c->sms;
+    p->glob_grid = slots;
+  }
+  return GSOFA_OK;
+}
+
+int check_options(const gsofa_options* in, gsofa_options* o) {
+  gsofa_default_options(o);
+  if (!in) return GSOFA_OK;
+  if (in->chunk_size < 0 || in->threads_per_source < 0 || in->smem_max_source < -1 ||
+      in->max_concurrent < 0 || in->mem_budget_bytes < 0)
+    return GSOFA_E_INVAL;
+  if (in->chunk_size) o->chunk_size = in->chunk_size;
+  if (in->threads_per_source) {
+    if (in->threads_per_source % 32 || in->threads_per_source < 64 || in->threads_per_source > 1024)
+      return GSOFA_E_INVAL;
+    o->threads_per_source = in->threads_per_source;
+  }
+  o->smem_max_source = in->smem_max_source;
+  o->max_concurrent = in->max_concurrent;
+  o->mem_budget_bytes = in->mem_budget_bytes;
+  o->fill_first = in->fill_first ? 1 : 0;
+  o->collect_stats = in->collect_stats ? 1 : 0;
+  o->validate = in->validate;
+  if (o->chunk_size > 1024) return GSOFA_E_INVAL;
+  return GSOFA_OK;
+}
+
+// ---------------------------------------------------------------- one matrix
+int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx, const gsofa_options& o,
+               cudaStream_t st, gsofa_result* out) {
+  zero_result(out);
+  Priv* pv = new Priv();
+  pv->stream = st;
+  pv->device = c->device;
+  pv->mpool = c->mpool;
+  out->_priv = pv;
+  out->n = n;
+  out->on_device = 1;
+  out->err_detail = -1;
+
+  Events ev;
+  ev.create(o.collect_stats != 0);
+  ev.rec(0, st);
+
+  int rc = GSOFA_OK;
+  cudaError_t ce = cudaSuccess;
+  DevCounters* ctr = nullptr;
+  int32_t* order = nullptr;
+  uint32_t* pool = nullptr;
+  int64_t* row_off = nullptr;
+  int32_t *row_nL = nullptr, *row_nU = nullptr, *flags = nullptr;
+  void* scan_tmp = nullptr;
+  int64_t* flag_pos = nullptr;
+  DevCounters* h = pinned_counters();
+  Plan plan;
+  long long pool_cap = 0;
+  bool have_global_lock = false;
+  int nlaunch = 0;
+  std::unique_lock<std::mutex> glk(c->gmu, std::defer_lock);
+
+#define CK(x)                        \
+  do {                               \
+    ce = (x);                        \
+    if (ce != cudaSuccess) {         \
+      rc = GSOFA_E_CUDA;             \
+      goto fail;                     \
+    }                                \
+  } while (0)
+#define LK(x)                        \
+  do {                               \
+    CK(x);                           \
+    nlaunch++;                       \
+  } while (0)
+
+  if (!h) { rc = GSOFA_E_NOMEM; goto fail; }
+  rc = make_plan(c, n, o, &plan);
+  if (rc) goto fail;
+
+  CK(palloc(c, &ctr, 1, st));
+  CK(palloc(c, &order, (size_t)n, st));
+  CK(palloc(c, &row_off, (size_t)n, st));
+  CK(palloc(c, &row_nL, (size_t)n, st));
+  CK(palloc(c, &row_nU, (size_t)n, st));
+  CK(palloc(c, &flags, (size_t)n, st));
+  CK(palloc(c, &out->fill_count, (size_t)n, st));
+  {
+    std::lock_guard<std::mutex> lk(c->hmu);
+    auto it = c->pool_hint.find(n);
+    pool_cap = it != c->pool_hint.end() ? it->second : (long long)256 * n + (1 << 20);
+    const long long full = (long long)n * (long long)(n + 1);
+    if (pool_cap > full) pool_cap = full;
+    if (pool_cap < 1024) pool_cap = 1024;
+  }
+  CK(palloc(c, &pool, (size_t)pool_cap, st));
+  // order: shared tier [S-1 .. 0] then global tier [n-1 .. S] (largest source first)
+  LK(launch_iota_desc(order, plan.S, plan.S, st));
+  LK(launch_iota_desc(order + plan.S, n, n - plan.S, st));
+
+  if (plan.S < n) {
+    glk.lock();
+    have_global_lock = true;
+    if (o.mem_budget_bytes > 0) {
+      const long long per_slot = 12LL * n + 8LL * ((n + 31) / 32);
+      const long long need = per_slot * plan.glob_grid + 4LL * pool_cap + 24LL * n;
+      if (need > o.mem_budget_bytes) {
+        long long slots = (o.mem_budget_bytes - 4LL * pool_cap - 24LL * n) / per_slot;
+        if (slots < 1) { rc = GSOFA_E_NOMEM; goto fail; }
+        plan.glob_grid = (int)slots;
+      }
+    }
+    rc = ensure_slots(c, n, plan.glob_grid, st);
+    if (rc) goto fail;
+    CK(cudaStreamWaitEvent(st, c->g_done, 0));
+  }
+
+  for (int attempt = 0; attempt < 3; attempt++) {
+    LK(launch_init_counters(ctr, st));
+    if (o.validate != 2 && attempt == 0) {
+      ev.rec(1, st);
+      LK(launch_validate(n, d_rowptr, d_colidx, ctr, st));
+    } else {
+      ev.rec(1, st);
+    }
+    TravArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.rowptr = d_rowptr;
+    a.colidx = d_colidx;
+    a.pool = pool;
+    a.pool_cap = pool_cap;
+    a.row_off = row_off;
+    a.row_nL = row_nL;
+    a.row_nU = row_nU;
+    a.fill_count = out->fill_count;
+    a.ctr = ctr;
+    a.fill_first = o.fill_first;
+    a.collect_stats = o.collect_stats;
+    ev.rec(2, st);
+    if (plan.S < n) {
+      a.order = order + plan.S;
+      a.nsrc = n - plan.S;
+      a.g_lab = c->g_lab;
+      a.g_queue = c->g_queue;
+      a.g_inq = c->g_inq;
+      a.g_rowbits = c->g_rowbits;
+      a.g_base = c->g_base;
+      a.g_cap = c->g_cap;
+      LK(launch_trav_global(a, plan.glob_grid, plan.glob_block, st));
+      CK(cudaEventRecord(c->g_done, st));
+    }
+    ev.rec(3, st);
+    if (plan.S > 0) {
+      a.order = order;
+      a.nsrc = plan.S;
+      a.S = plan.S;
+      LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, st));
+    }
+    ev.rec(4, st);
+    LK(launch_supernode_flags(n, o.chunk_size, pool, row_off, row_nL, row_nU, flags, ctr, st));
+    ev.rec(5, st);
+    CK(cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    rc = wait_stream(st);
+    if (rc) goto fail;
+    if (h->err & ERR_INPUT) {
+      rc = GSOFA_E_INVAL;
+      out->err_detail = h->err_row == INT_MAX ? -1 : h->err_row;
+      goto fail;
+    }
+    if (h->err & ERR_NOCONV) { rc = GSOFA_E_NOCONVERGE; goto fail; }
+    if (!(h->err & ERR_OVERFLOW)) break;
+    // the pool was too small: the counts are exact now, grow it and run again
+    out->stats.pool_retries++;
+    pfree(pool, st);
+    pool_cap = (long long)h->pool_cursor + 1024;
+    CK(palloc(c, &pool, (size_t)pool_cap, st));
+  }
+  if (h->err & ERR_OVERFLOW) { rc = GSOFA_E_NOMEM; goto fail; }
+  if (have_global_lock) { glk.unlock(); have_global_lock = false; }
+  {
+    std::lock_guard<std::mutex> lk(c->hmu);
+    c->pool_hint[n] = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
+  }
+
+  out->nnz_L = (int64_t)h->total_L;
+  out->nnz_U = (int64_t)h->total_U;
+  out->n_super = h->n_super;
+  out->stats.vertices_expanded = (int64_t)h->expansions;
+  out->stats.edges_scanned = (int64_t)h->edges;
+  out->stats.traverse_launches = (plan.S > 0) + (plan.S < n);
+
+  CK(palloc(c, &out->L_rowptr, (size_t)n + 1, st));
+  CK(palloc(c, &out->U_rowptr, (size_t)n + 1, st));
+  CK(palloc(c, &out->L_colidx, (size_t)out->nnz_L, st));
+  CK(palloc(c, &out->U_colidx, (size_t)out->nnz_U, st));
+  CK(palloc(c, &out->super_start, (size_t)out->n_super + 1, st));
+  CK(palloc(c, &flag_pos, (size_t)n + 1, st));
+  {
+    size_t tb = scan_tmp_bytes(n);
+    CK(cudaMallocFromPoolAsync(&scan_tmp, tb, c->mpool, st));
+  }
+  CK(launch_scan_i32_i64(row_nL, out->L_rowptr, n, scan_tmp, st));
+  CK(launch_scan_i32_i64(row_nU, out->U_rowptr, n, scan_tmp, st));
+  if (n > 0) nlaunch += 9;  // three scans of three kernels each
+  LK(launch_compact(n, pool, row_off, row_nL, row_nU, out->L_rowptr, out->U_rowptr, out->L_colidx,
+                    out->U_colidx, st));
+  CK(launch_scan_i32_i64(flags, flag_pos, n, scan_tmp, st));
+  LK(launch_scatter_starts(n, flags, flag_pos, out->super_start, st));
+  ev.rec(6, st);
+  out->stats.kernel_launches = nlaunch;
+
+  pfree(ctr, st);
+  pfree(order, st);
+  pfree(pool, st);
+  pfree(row_off, st);
+  pfree(row_nL, st);
+  pfree(row_nU, st);
+  pfree(flags, st);
+  pfree(flag_pos, st);
+  if (scan_tmp) cudaFreeAsync(scan_tmp, st);
+  scan_tmp = nullptr;
+
+  if (o.collect_stats) {
+    rc = wait_stream(st);
+    if (rc) goto fail;
+    out->stats.ms_validate = ev.ms(1, 2);
+    out->stats.ms_traverse_global = ev.ms(2, 3);
+    out->stats.ms_traverse_smem = ev.ms(3, 4);
+    out->stats.ms_traverse = ev.ms(2, 4);
+    out->stats.ms_supernode = ev.ms(4, 5);
+    out->stats.ms_emit = ev.ms(5, 6);
+    out->stats.ms_total = ev.ms(0, 6);
+  }
+  if (cudaGetLastError() != cudaSuccess) { rc = GSOFA_E_CUDA; goto fail; }
+  return GSOFA_OK;
+
+fail:
+  cudaGetLastError();
+  if (have_global_lock) glk.unlock();
+  wait_stream(st);
+  pfree(ctr, st);
+  pfree(order, st);
+  pfree(pool, st);
+  pfree(row_off, st);
+  pfree(row_nL, st);
+  pfree(row_nU, st);
+  pfree(flags, st);
+  pfree(flag_pos, st);
+  if (scan_tmp) cudaFreeAsync(scan_tmp, st);
+  {
+    const int32_t det = out->err_detail;
+    gsofa_free(out);
+    out->err_detail = det;
+  }
+  return rc;
+#undef CK
+}
+
+}  // namespace
+}  // namespace gsofa
+
+using namespace gsofa;
+
+extern "C" {
+
+int gsofa_version(void) { return 10000; }
+
+const char* gsofa_strerror(int code) {
+  switch (code) {
+    case GSOFA_OK: return "ok";
+    case GSOFA_E_INVAL: return "invalid argument or malformed CSR";
+    case GSOFA_E_NOMEM: return "out of memory or memory budget too small";
+    case GSOFA_E_CUDA: return "CUDA runtime error";
+    case GSOFA_E_NOCONVERGE: return "traversal iteration cap reached";
+    case GSOFA_E_TIMEOUT: return "bounded wait timed out";
+    case GSOFA_E_BUSY: return "admission queue full";
+    case GSOFA_E_NOTFOUND: return "unknown ticket";
+    case GSOFA_E_PENDING: return "request still pending";
+    default: return "unknown error";
+  }
+}
+
+int gsofa_default_options(gsofa_options* opt) {
+  if (!opt) return GSOFA_E_INVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->chunk_size = 128;
+  opt->validate = 1;
+  return GSOFA_OK;
+}
+
+void gsofa_free(gsofa_result* res) {
+  if (!res) return;
+  Priv* pv = (Priv*)res->_priv;
+  if (res->on_device) {
+    cudaStream_t st = pv ? pv->stream : nullptr;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (pv && cur != pv->device) cudaSetDevice(pv->device);
+    pfree(res->L_rowptr, st);
+    pfree(res->L_colidx, st);
+    pfree(res->U_rowptr, st);
+    pfree(res->U_colidx, st);
+    pfree(res->fill_count, st);
+    pfree(res->super_start, st);
+    if (pv && cur != pv->device && cur >= 0) cudaSetDevice(cur);
+  } else if (pv) {
+    pinned_put(pv->host_block, pv->host_cap);
+  }
+  delete pv;
+  std::memset(res, 0, sizeof(*res));
+}
+
+int gsofa_symbolic_device(int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx,
+                          const gsofa_options* opt, void* stream, gsofa_result* out) {
+  if (!out) return GSOFA_E_INVAL;
+  zero_result(out);
+  out->err_detail = -1;
+  gsofa_options o;
+  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
+  if (n < 0 || !d_rowptr || (n > 0 && !d_colidx)) return GSOFA_E_INVAL;
+  if (n > INT32_MAX - 2) return GSOFA_E_INVAL;
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return err;
+  return run_device(c, n, d_rowptr, d_colidx, o, (cudaStream_t)stream, out);
+}
+
+int gsofa_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colidx, const gsofa_options* opt,
+                   gsofa_result* out) {
+  if (!out) return GSOFA_E_INVAL;
+  zero_result(out);
+  out->err_detail = -1;
+  if (n < 0 || !rowptr || (n > 0 && !colidx)) return GSOFA_E_INVAL;
+  if (rowptr[0] != 0 || rowptr[n] < 0) { out->err_detail = 0; return GSOFA_E_INVAL; }
+  gsofa_options o;
+  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return err;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return GSOFA_E_CUDA;
+  const int64_t nnz = rowptr[n];
+  int32_t *d_rp = nullptr, *d_ci = nullptr;
+  gsofa_result dres;
+  zero_result(&dres);
+  int rc = GSOFA_OK;
+  if (palloc(c, &d_rp, (size_t)n + 1, st) != cudaSuccess || palloc(c, &d_ci, (size_t)nnz, st) != cudaSuccess) {
+    rc = GSOFA_E_NOMEM;
+  } else if (cudaMemcpyAsync(d_rp, rowptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess ||
+             (nnz > 0 && cudaMemcpyAsync(d_ci, colidx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                         st) != cudaSuccess)) {
+    rc = GSOFA_E_CUDA;
+  } else {
+    rc = run_device(c, n, d_rp, d_ci, o, st, &dres);
+  }
+  if (rc == GSOFA_OK) {
+    out->n = n;
+    out->n_super = dres.n_super;
+    out->nnz_L = dres.nnz_L;
+    out->nnz_U = dres.nnz_U;
+    out->stats = dres.stats;
+    out->on_device = 0;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_rp = al(8 * ((size_t)n + 1)), b_lc = al(4 * (size_t)dres.nnz_L + 4),
+                 b_uc = al(4 * (size_t)dres.nnz_U + 4), b_fc = al(4 * (size_t)n + 4),
+                 b_ss = al(4 * ((size_t)dres.n_super + 1));
+    Priv* hp = new Priv();
+    hp->device = c->device;
+    out->_priv = hp;
+    char* blk = (char*)pinned_get(2 * b_rp + b_lc + b_uc + b_fc + b_ss, &hp->host_cap);
+    hp->host_block = blk;
+    if (!blk) {
+      rc = GSOFA_E_NOMEM;
+    } else {
+      out->L_rowptr = (int64_t*)blk;
+      out->U_rowptr = (int64_t*)(blk + b_rp);
+      out->L_colidx = (int32_t*)(blk + 2 * b_rp);
+      out->U_colidx = (int32_t*)(blk + 2 * b_rp + b_lc);
+      out->fill_count = (int32_t*)(blk + 2 * b_rp + b_lc + b_uc);
+      out->super_start = (int32_t*)(blk + 2 * b_rp + b_lc + b_uc + b_fc);
+      cudaError_t e = cudaSuccess;
+      e = e ? e : cudaMemcpyAsync(out->L_rowptr, dres.L_rowptr, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st);
+      e = e ? e : cudaMemcpyAsync(out->U_rowptr, dres.U_rowptr, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost, st);
+      if (dres.nnz_L > 0)
+        e = e ? e : cudaMemcpyAsync(out->L_colidx, dres.L_colidx, 4 * (size_t)dres.nnz_L, cudaMemcpyDeviceToHost, st);
+      if (dres.nnz_U > 0)
+        e = e ? e : cudaMemcpyAsync(out->U_colidx, dres.U_colidx, 4 * (size_t)dres.nnz_U, cudaMemcpyDeviceToHost, st);
+      if (n > 0)
+        e = e ? e : cudaMemcpyAsync(out->fill_count, dres.fill_count, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
+      e = e ? e : cudaMemcpyAsync(out->super_start, dres.super_start, 4 * ((size_t)dres.n_super + 1),
+                                  cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) rc = GSOFA_E_CUDA;
+      const int w = wait_stream(st);
+      if (rc == GSOFA_OK) rc = w;
+    }
+  } else {
+    out->err_detail = dres.err_detail;
+  }
+  gsofa_free(&dres);
+  pfree(d_rp, st);
+  pfree(d_ci, st);
+  wait_stream(st);
+  cudaStreamDestroy(st);
+  if (rc != GSOFA_OK) {
+    const int32_t det = out->err_detail;
+    gsofa_free(out);
+    out->err_detail = det;
+  }
+  return rc;
+}
+
+int gsofa_batch(int32_t count, const int32_t* n, const int32_t* const* d_rowptr, const int32_t* const* d_colidx,
+                const gsofa_options* opt, void* stream, gsofa_result* outs) {
+  if (count < 0 || (count > 0 && (!n || !d_rowptr || !d_colidx || !outs))) return GSOFA_E_INVAL;
+  for (int32_t k = 0; k < count; k++) {
+    const int rc = gsofa_symbolic_device(n[k], d_rowptr[k], d_colidx[k], opt, stream, &outs[k]);
+    if (rc != GSOFA_OK) {
+      for (int32_t j = 0; j < k; j++) gsofa_free(&outs[j]);
+      return rc;
+    }
+  }
+  return GSOFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// CSR validation, prefix sums, row compaction and supernode detection.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace gsofa {
+
+namespace {
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER_THREAD = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
+
+__device__ __forceinline__ void flag_row(DevCounters* c, int bit, int row) {
+  atomicOr(&c->err, bit);
+  atomicMin(&c->err_row, row);
+}
+}  // namespace
+
+// ---------------------------------------------------------------- validate
+// One warp per row: rowptr[0] == 0, rowptr non-decreasing, 0 <= col < n and
+// columns strictly increasing inside every row (Section 2.4 uses CSR input).
+__global__ void validate_kernel(int32_t n, const int32_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ colidx, DevCounters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  if (gw == 0 && lane == 0 && rowptr[0] != 0) flag_row(ctr, ERR_ROWPTR, 0);
+  for (int i = gw; i < n; i += nw) {
+    const int rb = rowptr[i], re = rowptr[i + 1];
+    if (re < rb || rb < 0) {
+      if (lane == 0) flag_row(ctr, ERR_ROWPTR, i);
+      continue;
+    }
+    bool bad_range = false, bad_order = false;
+    for (int e = rb + lane; e < re; e += 32) {
+      const int c = colidx[e];
+      if ((unsigned)c >= (unsigned)n) bad_range = true;
+      if (e > rb && colidx[e - 1] >= c) bad_order = true;
+    }
+    if (__any_sync(FULL, bad_range) && lane == 0) flag_row(ctr, ERR_COL_RANGE, i);
+    if (__any_sync(FULL, bad_order) && lane == 0) flag_row(ctr, ERR_UNSORTED, i);
+  }
+}
+
+__global__ void init_counters_kernel(DevCounters* c) {
+  if (threadIdx.x == 0) {
+    c->pool_cursor = 0ull;
+    c->total_L = 0ull;
+    c->total_U = 0ull;
+    c->expansions = 0ull;
+    c->edges = 0ull;
+    c->err = 0;
+    c->err_row = INT_MAX;
+    c->n_super = 0;
+    c->work_smem = 0;
+    c->work_global = 0;
+  }
+}
+
+cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,
+                            DevCounters* ctr, cudaStream_t st) {
+  const int block = 256;
+  long long warps = n > 0 ? n : 1;
+  long long grid = (warps * 32 + block - 1) / block;
+  if (grid > 4096) grid = 4096;
+  validate_kernel<<<(int)grid, block, 0, st>>>(n, rowptr, colidx, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st) {
+  init_counters_kernel<<<1, 32, 0, st>>>(c);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- scan
+// out[0] = 0, out[i+1] = in[0] + ... + in[i]  (int32 in, int64 out)
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long y = lane < nw ? sh[lane] : 0;
+    long long z = y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(FULL, z, o);
+      if (lane >= o) z += t;
+    }
+    if (lane < nw) sh[lane] = z - y;
+    if (lane == 31) sh[32] = z;
+  }
+  __syncthreads();
+  const long long r = sh[warp] + x - v;
+  *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int32_t n, long long* part) {
+  __shared__ long long sh[33];
+  const long long base = (long long)blockIdx.x * SCAN_TILE;
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; k++) {
+    const long long i = base + (long long)threadIdx.x * SCAN_PER_THREAD + k;
+    if (i < n) s += in[i];
+  }
+  long long tot;
+  block_excl_scan(s, sh, &tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void scan_parts_kernel(long long* part, int32_t nparts) {
+  __shared__ long long sh[33];
+  long long carry = 0;
+  for (int b0 = 0; b0 < nparts; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const long long v = b < nparts ? part[b] : 0;
+    long long tot;
+    const long long ex = block_excl_scan(v, sh, &tot);
+    if (b < nparts) part[b] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void scan_down_kernel(const int32_t* __restrict__ in, int32_t n, const long long* part,
+                                 int64_t* out) {
+  __shared__ long long sh[33];
+  const long long base = (long long)blockIdx.x * SCAN_TILE;
+  int32_t v[SCAN_PER_THREAD];
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; k++) {
+    const long long i = base + (long long)threadIdx.x * SCAN_PER_THREAD + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  long long tot;
+  long long ex = block_excl_scan(s, sh, &tot) + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; k++) {
+    const long long i = base + (long long)threadIdx.x * SCAN_PER_THREAD + k;
+    if (i < n) out[i] = ex;
+    ex += v[k];
+    if (i == (long long)n - 1) out[n] = ex;
+  }
+}
+
+size_t scan_tmp_bytes(int32_t n) {
+  const long long parts = ((long long)n + SCAN_TILE - 1) / SCAN_TILE;
+  return (size_t)(parts > 0 ? parts : 1) * sizeof(long long);
+}
+
+cudaError_t launch_scan_i32_i64(const int32_t* in, int64_t* out, int32_t n, void* tmp, cudaStream_t st) {
+  if (n <= 0) {
+    return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+  }
+  const int parts = (int)(((long long)n + SCAN_TILE - 1) / SCAN_TILE);
+  long long* part = (long long*)tmp;
+  scan_reduce_kernel<<<parts, SCAN_THREADS, 0, st>>>(in, n, part);
+  scan_parts_kernel<<<1, SCAN_THREADS, 0, st>>>(part, parts);
+  scan_down_kernel<<<parts, SCAN_THREADS, 0, st>>>(in, n, part, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- compact
+// Move every row from the pool ([L cols | s | U cols] at row_off) to its CSR slot.
+__global__ void compact_kernel(int32_t n, const uint32_t* __restrict__ pool,
+                               const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_nL,
+                               const int32_t* __restrict__ row_nU, const int64_t* __restrict__ L_rowptr,
+                               const int64_t* __restrict__ U_rowptr, int32_t* __restrict__ L_colidx,
+                               int32_t* __restrict__ U_colidx) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < n; i += nw) {
+    const int64_t off = row_off[i];
+    const int nL = row_nL[i], nU = row_nU[i];
+    const uint32_t* src = pool + off;
+    int32_t* dL = L_colidx + L_rowptr[i];
+    int32_t* dU = U_colidx + U_rowptr[i];
+    for (int k = lane; k < nL; k += 32) dL[k] = (int32_t)__ldcs(src + k);
+    for (int k = lane; k < nU; k += 32) dU[k] = (int32_t)__ldcs(src + nL + k);
+  }
+}
+
+cudaError_t launch_compact(int32_t n, const uint32_t* pool, const int64_t* row_off,
+                           const int32_t* row_nL, const int32_t* row_nU, const int64_t* L_rowptr,
+                           const int64_t* U_rowptr, int32_t* L_colidx, int32_t* U_colidx,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = ((long long)n * 32 + block - 1) / block;
+  if (grid > 152 * 16) grid = 152 * 16;
+  compact_kernel<<<(int)grid, block, 0, st>>>(n, pool, row_off, row_nL, row_nU, L_rowptr, U_rowptr,
+                                              L_colidx, U_colidx);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- supernodes
+// Two-phase T3 detection (Section 5, Fig. 7), one CTA per aligned chunk.
+// Phase I : thread t tests nnz(U(s,:)) == nnz(U(s-1,:)) - 1 for row s = chunk
+//           start + t into a shared bitmap; rows that fail lead a run.
+// Phase II: every leading row walks its run: row s stays in the supernode
+//           that starts at r while its bit is set and L(s, r) != 0 (binary
+//           search in the sorted L row); otherwise s starts a new supernode.
+// flags[s] = 1 iff s is the first row of a supernode.
+__global__ void supernode_kernel(int32_t n, int32_t chunk, const uint32_t* __restrict__ pool,
+                                 const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_nL,
+                                 const int32_t* __restrict__ row_nU, int32_t* __restrict__ flags,
+                                 DevCounters* ctr) {
+  extern __shared__ uint32_t bits[];  // ceil(chunk/32) words
+  __shared__ int s_count;
+  const int c0 = blockIdx.x * chunk;
+  const int cend = min(n, c0 + chunk);
+  const int nwords = (chunk + 31) >> 5;
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0u;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; c0 + t < cend; t += blockDim.x) {
+    const int s = c0 + t;
+    if (t > 0 && row_nU[s] == row_nU[s - 1] - 1) atomicOr(&bits[t >> 5], 1u << (t & 31));
+  }
+  __syncthreads();
+  int local = 0;
+  for (int t = threadIdx.x; c0 + t < cend; t += blockDim.x) {
+    if (bits[t >> 5] & (1u << (t & 31))) continue;  // not a leading row
+    int r = c0 + t;
+    flags[r] = 1;
+    local++;
+    for (int u = t + 1; c0 + u < cend && (bits[u >> 5] & (1u << (u & 31))); u++) {
+      const int s = c0 + u;
+      const int64_t off = row_off[s];
+      bool has = false;
+      if (off >= 0) {
+        int lo = 0, hi = row_nL[s];
+        const uint32_t key = (uint32_t)r;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          const uint32_t x = pool[off + mid];
+          if (x < key) lo = mid + 1; else hi = mid;
+        }
+        has = lo < row_nL[s] && pool[off + lo] == key;
+      }
+      if (has) {
+        flags[s] = 0;
+      } else {
+        flags[s] = 1;
+        r = s;
+        local++;
+      }
+    }
+  }
+  if (local) atomicAdd(&s_count, local);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_count) atomicAdd(&ctr->n_super, s_count);
+}
+
+cudaError_t launch_supernode_flags(int32_t n, int32_t chunk, const uint32_t* pool, const int64_t* row_off,
+                                   const int32_t* row_nL, const int32_t* row_nU, int32_t* flags,
+                                   DevCounters* ctr, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nchunks = (int)(((long long)n + chunk - 1) / chunk);
+  const int block = chunk >= 1024 ? 1024 : ((chunk + 31) / 32) * 32;
+  const size_t sm = (size_t)((chunk + 31) / 32) * 4;
+  supernode_kernel<<<nchunks, block, sm, st>>>(n, chunk, pool, row_off, row_nL, row_nU, flags, ctr);
+  return cudaGetLastError();
+}
+
+__global__ void scatter_starts_kernel(int32_t n, const int32_t* __restrict__ flags,
+                                      const int64_t* __restrict__ pos, int32_t* __restrict__ super_start) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (flags[i]) super_start[pos[i]] = (int32_t)i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) super_start[pos[n]] = n;
+}
+
+cudaError_t launch_scatter_starts(int32_t n, const int32_t* flags, const int64_t* pos,
+                                  int32_t* super_start, cudaStream_t st) {
+  const int block = 256;
+  long long grid = ((long long)(n > 0 ? n : 1) + block - 1) / block;
+  if (grid > 4096) grid = 4096;
+  scatter_starts_kernel<<<(int)grid, block, 0, st>>>(n, flags, pos, super_start);
+  return cudaGetLastError();
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int64_t count, int32_t v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = (count + block - 1) / block;
+  if (grid > 4096) grid = 4096;
+  fill_i32_kernel<<<(int)grid, block, 0, st>>>(p, count, v);
+  return cudaGetLastError();
+}
+
+__global__ void iota_desc_kernel(int32_t* out, int32_t hi, int32_t count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = hi - 1 - (int32_t)i;
+}
+
+cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = ((long long)count + block - 1) / block;
+  if (grid > 4096) grid = 4096;
+  iota_desc_kernel<<<(int)grid, block, 0, st>>>(out, hi, count);
+  return cudaGetLastError();
+}
+
+}  // namespace gsofa

@@ -1,0 +1,96 @@
+// Internal declarations shared by the CUDA translation units of libgsofa.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gsofa {
+
+// ---- device error word bits (err[0]); err[1] keeps the first offending row
+enum : int32_t {
+  ERR_COL_RANGE = 1,   // a column index outside [0, n)
+  ERR_ROWPTR = 2,      // rowptr[0] != 0, decreasing rowptr, or rowptr[n] inconsistent
+  ERR_UNSORTED = 4,    // columns not strictly increasing inside a row
+  ERR_NOCONV = 8,      // traversal iteration cap reached
+  ERR_OVERFLOW = 16,   // row pool too small (the host grows it and reruns)
+  ERR_INPUT = ERR_COL_RANGE | ERR_ROWPTR | ERR_UNSORTED,
+};
+
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Counters in one small device block so one copy brings them back.
+struct DevCounters {
+  unsigned long long pool_cursor;   // entries requested from the row pool
+  unsigned long long total_L;       // sum of nnz(L(i,:))
+  unsigned long long total_U;       // sum of nnz(U(i,:)) (diagonal included)
+  unsigned long long expansions;    // frontier expansions (stats)
+  unsigned long long edges;         // adjacency entries read (stats)
+  int32_t err;                      // ERR_* bits
+  int32_t err_row;                  // first offending row (atomicMin), INT32_MAX if none
+  int32_t n_super;                  // supernodes found
+  int32_t work_smem;                // work counter of the shared-memory tier
+  int32_t work_global;              // work counter of the global tier
+  int32_t pad[3];
+};
+
+// Input errors found so far (read through L2, not a cached copy).
+__device__ __forceinline__ int input_error(const DevCounters* c) {
+  return *(const volatile int32_t*)&c->err & ERR_INPUT;
+}
+
+// Arguments of the traversal kernels (Section 4, Fig. 5).
+struct TravArgs {
+  int32_t n;
+  const int32_t* __restrict__ rowptr;
+  const int32_t* __restrict__ colidx;
+  const int32_t* __restrict__ order;  // source rows to process, in order of issue
+  int32_t nsrc;
+  int32_t S;                          // shared tier: label capacity (all sources < S)
+  uint32_t* pool;                     // row pool: per source [L cols | s | U cols]
+  int64_t pool_cap;                   // entries
+  int64_t* row_off;                   // per row: pool offset (-1 if it did not fit)
+  int32_t* row_nL;
+  int32_t* row_nU;
+  int32_t* fill_count;
+  DevCounters* ctr;
+  int32_t fill_first;                 // optional "line 9.5" of Section 4
+  int32_t collect_stats;
+  // global tier: per-slot working arrays (slot = CTA index)
+  uint32_t* g_lab;                    // slots x n (epoch-encoded maxId)
+  int32_t* g_queue;                   // slots x 2n (current / next frontier)
+  uint32_t* g_inq;                    // slots x ceil(n/32) (dedup of the next frontier)
+  uint32_t* g_rowbits;                // slots x ceil(n/32) (columns of the row found so far)
+  uint32_t* g_base;                   // per slot: current maxId window base (persists across launches)
+  int64_t g_cap;                      // per-slot capacity in vertices (>= n)
+};
+
+// ---- launchers (return cudaGetLastError())
+size_t trav_smem_bytes(int32_t n, int32_t S);
+int32_t trav_smem_max_S(int32_t n, size_t smem_limit);
+cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, cudaStream_t st);
+size_t trav_global_smem_bytes(int32_t n);
+cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st);
+
+cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,
+                            DevCounters* ctr, cudaStream_t st);
+
+// exclusive scan of int32 counts into int64 offsets (out has n+1 entries)
+size_t scan_tmp_bytes(int32_t n);
+cudaError_t launch_scan_i32_i64(const int32_t* in, int64_t* out, int32_t n, void* tmp,
+                                cudaStream_t st);
+cudaError_t launch_compact(int32_t n, const uint32_t* pool, const int64_t* row_off,
+                           const int32_t* row_nL, const int32_t* row_nU,
+                           const int64_t* L_rowptr, const int64_t* U_rowptr,
+                           int32_t* L_colidx, int32_t* U_colidx, cudaStream_t st);
+cudaError_t launch_supernode_flags(int32_t n, int32_t chunk, const uint32_t* pool,
+                                   const int64_t* row_off, const int32_t* row_nL,
+                                   const int32_t* row_nU, int32_t* flags, DevCounters* ctr,
+                                   cudaStream_t st);
+cudaError_t launch_scatter_starts(int32_t n, const int32_t* flags, const int64_t* pos,
+                                  int32_t* super_start, cudaStream_t st);
+cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t st);
+cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
+cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
+
+}  // namespace gsofa
