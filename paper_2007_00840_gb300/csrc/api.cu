@@ -21,8 +21,6 @@
 
 namespace gsofa {
 
-int trav_smem_static_bytes();                    // traverse_smem.cu
-int trav_smem_occupancy(int block, size_t dyn_bytes);  // traverse_smem.cu
 
 namespace {
 
@@ -237,29 +235,64 @@ void zero_result(gsofa_result* out) { std::memset(out, 0, sizeof(*out)); }
 
 struct Plan {
   int32_t S = 0;          // shared tier: sources [0, S)
+  int label16 = 0;        // shared tier: 16-bit maxId
+  int32_t list_cap = 0;   // shared tier: frontier list entries held on chip
   int smem_block = 512;
   int smem_grid = 0;
   int glob_block = 512;
   int glob_grid = 0;
 };
 
+// Shared tier: largest S that fits one CTA, then the (block, CTAs per SM) pair
+// with the most resident threads (ties: more CTAs, i.e. more sources in
+// flight), then the largest frontier list that keeps that occupancy.
 int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   const int stat = trav_smem_static_bytes();
+  const int label16 = n <= 65533 ? 1 : 0;
   const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
-  int32_t S = trav_smem_max_S(n, limit);
+  int32_t S = trav_smem_max_S(n, limit, label16);
   if (o.smem_max_source > 0 && o.smem_max_source < S) S = o.smem_max_source;
   if (o.smem_max_source < 0) S = 0;  // every source in the global tier
   if (S > n) S = n;
   if (S < 0) S = 0;
   p->S = S;
+  p->label16 = label16;
   if (S > 0) {
-    const size_t bytes = trav_smem_bytes(n, S);
-    int block = o.threads_per_source;
-    if (block <= 0) block = bytes > (size_t)c->smem_optin / 2 ? 1024 : 512;
-    p->smem_block = block;
-    int occ = trav_smem_occupancy(block, bytes);
-    if (occ < 1) return GSOFA_E_CUDA;
-    p->smem_grid = c->sms * occ;
+    const int32_t min_cap = S < 1024 ? S : 1024;
+    const size_t per_sm = 233472;  // 228 KB of shared memory per SM
+    int best_block = 0, best_occ = 0;
+    const int blocks[3] = {1024, 512, 256};
+    for (int bi = 0; bi < 3; bi++) {
+      const int b = blocks[bi];
+      if (o.threads_per_source > 0 && b != o.threads_per_source) continue;
+      const int occ = trav_smem_occupancy(b, trav_smem_bytes(n, S, min_cap, label16), label16);
+      if (occ < 1) continue;
+      if (occ * b > best_occ * best_block || (occ * b == best_occ * best_block && occ > best_occ)) {
+        best_block = b;
+        best_occ = occ;
+      }
+    }
+    if (o.threads_per_source > 0 && best_block == 0) {
+      const int b = o.threads_per_source;
+      const int occ = trav_smem_occupancy(b, trav_smem_bytes(n, S, min_cap, label16), label16);
+      if (occ >= 1) { best_block = b; best_occ = occ; }
+    }
+    if (best_block == 0) return GSOFA_E_CUDA;
+    // largest list capacity that keeps best_occ CTAs per SM
+    size_t lim = per_sm / (size_t)best_occ;
+    lim = lim > (size_t)stat + 1024 + 64 ? lim - (size_t)stat - 1024 - 64 : 0;
+    if (lim > limit) lim = limit;
+    int32_t cap = S;
+    const size_t esz = label16 ? 2 : 4;
+    const size_t fixed = trav_smem_bytes(n, S, 0, label16);
+    if (fixed + 2 * esz * (size_t)cap > lim) cap = lim > fixed ? (int32_t)((lim - fixed) / (2 * esz)) : 0;
+    cap &= ~31;
+    if (cap < min_cap) cap = min_cap;
+    while (cap > min_cap && trav_smem_occupancy(best_block, trav_smem_bytes(n, S, cap, label16), label16) < best_occ)
+      cap = (cap / 2 > min_cap) ? cap / 2 : min_cap;
+    p->list_cap = cap;
+    p->smem_block = best_block;
+    p->smem_grid = c->sms * best_occ;
   }
   if (S < n) {
     int block = o.threads_per_source > 0 ? o.threads_per_source : 512;
@@ -318,6 +351,8 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   int32_t *row_nL = nullptr, *row_nU = nullptr, *flags = nullptr;
   void* scan_tmp = nullptr;
   int64_t* flag_pos = nullptr;
+  int32_t* spill = nullptr;
+  int64_t spill_cap = 0;
   DevCounters* h = pinned_counters();
   Plan plan;
   long long pool_cap = 0;
@@ -359,6 +394,10 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     if (pool_cap < 1024) pool_cap = 1024;
   }
   CK(palloc(c, &pool, (size_t)pool_cap, st));
+  if (plan.S > 0) {
+    spill_cap = plan.S > plan.list_cap ? plan.S - plan.list_cap : 1;
+    CK(palloc(c, &spill, (size_t)plan.smem_grid * 2 * (size_t)spill_cap, st));
+  }
   // order: shared tier [S-1 .. 0] then global tier [n-1 .. S] (largest source first)
   LK(launch_iota_desc(order, plan.S, plan.S, st));
   LK(launch_iota_desc(order + plan.S, n, n - plan.S, st));
@@ -420,7 +459,10 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.order = order;
       a.nsrc = plan.S;
       a.S = plan.S;
-      LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, st));
+      a.list_cap = plan.list_cap;
+      a.spill = spill;
+      a.spill_cap = spill_cap;
+      LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, plan.label16, st));
     }
     ev.rec(4, st);
     LK(launch_supernode_flags(n, o.chunk_size, pool, row_off, row_nL, row_nU, flags, ctr, st));
@@ -483,6 +525,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   pfree(row_nU, st);
   pfree(flags, st);
   pfree(flag_pos, st);
+  pfree(spill, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   scan_tmp = nullptr;
 
@@ -512,6 +555,7 @@ fail:
   pfree(row_nU, st);
   pfree(flags, st);
   pfree(flag_pos, st);
+  pfree(spill, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   {
     const int32_t det = out->err_detail;

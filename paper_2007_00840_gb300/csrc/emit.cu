@@ -217,6 +217,8 @@ __global__ void supernode_kernel(int32_t n, int32_t chunk, const uint32_t* __res
                                  DevCounters* ctr) {
   extern __shared__ uint32_t bits[];  // ceil(chunk/32) words
   __shared__ int s_count;
+  // rejected input: the traversal wrote no rows, so there is nothing to read
+  if (input_error(ctr)) return;
   const int c0 = blockIdx.x * chunk;
   const int cend = min(n, c0 + chunk);
   const int nwords = (chunk + 31) >> 5;

@@ -47,6 +47,9 @@ struct TravArgs {
   const int32_t* __restrict__ order;  // source rows to process, in order of issue
   int32_t nsrc;
   int32_t S;                          // shared tier: label capacity (all sources < S)
+  int32_t list_cap;                   // shared tier: frontier list capacity in shared memory
+  int32_t* spill;                     // shared tier: per CTA 2 x spill_cap overflow entries
+  int64_t spill_cap;
   uint32_t* pool;                     // row pool: per source [L cols | s | U cols]
   int64_t pool_cap;                   // entries
   int64_t* row_off;                   // per row: pool offset (-1 if it did not fit)
@@ -66,9 +69,11 @@ struct TravArgs {
 };
 
 // ---- launchers (return cudaGetLastError())
-size_t trav_smem_bytes(int32_t n, int32_t S);
-int32_t trav_smem_max_S(int32_t n, size_t smem_limit);
-cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, cudaStream_t st);
+size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16);
+int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16);
+cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st);
+int trav_smem_static_bytes();
+int trav_smem_occupancy(int block, size_t dyn_bytes, int label16);
 size_t trav_global_smem_bytes(int32_t n);
 cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st);
 

@@ -19,6 +19,7 @@ namespace gsofa {
 namespace {
 
 constexpr int BIG_DEG = 32;
+constexpr int BATCH = 8;  // column loads issued together per frontier vertex
 
 struct GState {
   uint32_t* lab;
@@ -166,15 +167,22 @@ __global__ void __launch_bounds__(1024, 1) trav_global_kernel(TravArgs a) {
         uint32_t nmE = 0u;
         if (i < qlen) {
           v = qcur[i];
-          eb = a.rowptr[v];
-          ee = a.rowptr[v + 1];
+          eb = __ldg(a.rowptr + v);
+          ee = __ldg(a.rowptr + v + 1);
           const uint32_t lv = *(volatile uint32_t*)&lab[v];
           const uint32_t vE = base + 1u + (uint32_t)v;
           nmE = lv > vE ? lv : vE;
           n_exp++;
           if (ee - eb <= BIG_DEG) {
             n_edge += (unsigned long long)(ee - eb);
-            for (int e = eb; e < ee; e++) relax_g(g, a.colidx[e], nmE, &bad);
+            for (int e0 = eb; e0 < ee; e0 += BATCH) {
+              int wv[BATCH];  // independent loads first, then the relaxations
+#pragma unroll
+              for (int q = 0; q < BATCH; q++) wv[q] = (e0 + q < ee) ? __ldg(a.colidx + e0 + q) : 0;
+#pragma unroll
+              for (int q = 0; q < BATCH; q++)
+                if (e0 + q < ee) relax_g(g, wv[q], nmE, &bad);
+            }
           }
         }
         unsigned bigm = __ballot_sync(FULL, v >= 0 && (ee - eb) > BIG_DEG);
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(1024, 1) trav_global_kernel(TravArgs a) {
           const int beb = __shfl_sync(FULL, eb, l), bee = __shfl_sync(FULL, ee, l);
           const uint32_t bnm = __shfl_sync(FULL, nmE, l);
           if (lane == 0) n_edge += (unsigned long long)(bee - beb);
-          for (int e = beb + lane; e < bee; e += 32) relax_g(g, a.colidx[e], bnm, &bad);
+          for (int e = beb + lane; e < bee; e += 32) relax_g(g, __ldg(a.colidx + e), bnm, &bad);
         }
       }
       __syncthreads();

@@ -1,27 +1,33 @@
 // Multi-source maxId traversal, shared-memory tier (Section 4, Fig. 5).
 //
 // One CTA owns one source row s at a time and loops over sources from a global
-// work counter (persistent CTAs).  Per source it keeps, in shared memory:
+// work counter (persistent CTAs, largest source first).  Per source it keeps
+// in shared memory:
 //   lab[0..S)   maxId of every vertex below the source (bubble removal,
-//               Section 6: vertices above s never need one), stored with the
-//               value-range windows of Section 4 ("Optimizing the initialization
-//               of maxId"): source number k of this CTA uses the window
-//               [base_k, base_k + n + 1] with base_k decreasing, so anything
-//               above the window reads as "not reached" and lab[] is never
-//               cleared between sources;
-//   fA/fB       the current / next frontier as bitmaps over [0, s);
+//               Section 6: vertices above s never need one).  16-bit when the
+//               matrix order allows it, else 32-bit.  Values use the
+//               value-range windows of Section 4 ("Optimizing the
+//               initialization of maxId"): the k-th source of this CTA uses the
+//               window [base_k, base_k + s_k] with base_k decreasing, so any
+//               value above the window reads as "not reached" and lab[] is
+//               refilled only when the range is used up;
+//   list0/list1 the current and next frontier as compact lists; entries past
+//               the list capacity spill to a per-CTA area in global memory (the
+//               external frontier management of Section 6, one level down);
+//   D0/D1       dedup bitmaps: bit v of D[b] is set iff v is in list b;
 //   ub          the U part of the row as a bitmap over [0, n).
 // maxId of a vertex is the smallest "largest intermediate vertex" over the
 // paths found so far; a direct neighbour of s has no intermediate (-1).
 //
 // Level loop: every frontier vertex f proposes nm = max(maxId(f), f) to each
-// neighbour w (atomicMin).  If the proposal lowers maxId(w) and w was not
+// neighbour w (atomic min).  If the proposal lowers maxId(w) and w was not
 // already a fill (old > w), w's own proposal changed, so w joins the next
 // frontier; w is a fill of L(s,:) iff its final maxId < w (Theorem 1).
-// Neighbours above s are U entries.  The frontier of a level is expanded by all
-// warps in parallel; a warp turns 32 bitmap words into a compact list of
-// vertices with ballot/shuffle and expands them one vertex per lane, with
-// rows longer than 32 entries expanded by the whole warp.
+// Neighbours above s are U entries.  Lanes of a warp take consecutive list
+// entries; a warp walks the adjacency rows of its 32 vertices in lock-step,
+// issuing a batch of independent column loads per step, and appends newly
+// queued vertices with one shared-memory atomic per warp.  One barrier per
+// level.
 //
 // Emission writes the sorted row [L cols | s | U cols] to the row pool at an
 // offset taken with one atomicAdd, plus the row's counts and fill count.
@@ -32,22 +38,7 @@ namespace gsofa {
 namespace {
 
 constexpr int BIG_DEG = 32;
-
-__device__ __forceinline__ int nth_set_bit(uint32_t x, int k) {
-  // position of the k-th (0-based) set bit of x, by halving
-  int pos = 0;
-  int c = __popc(x & 0xFFFFu);
-  if (k >= c) { k -= c; x >>= 16; pos += 16; }
-  c = __popc(x & 0xFFu);
-  if (k >= c) { k -= c; x >>= 8; pos += 8; }
-  c = __popc(x & 0xFu);
-  if (k >= c) { k -= c; x >>= 4; pos += 4; }
-  c = __popc(x & 0x3u);
-  if (k >= c) { k -= c; x >>= 2; pos += 2; }
-  c = (int)(x & 1u);
-  if (k >= c) { pos += 1; }
-  return pos;
-}
+constexpr int BATCH = 8;  // column loads issued together per frontier vertex
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
@@ -58,76 +49,123 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-struct SmemState {
-  uint32_t* lab;
-  uint32_t* ub;
-  uint32_t base;
-  int32_t s;
-  int32_t n;
-  int32_t fill_first;
+template <typename LabT>
+struct LabOps;
+
+template <>
+struct LabOps<uint32_t> {
+  static constexpr uint32_t MAXV = 0xFFFFFFFFu;
+  static __device__ __forceinline__ uint32_t amin(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
 };
 
-// Relax edge (f -> w) with encoded proposal nmE.  Returns 1 if w was enqueued.
-__device__ __forceinline__ int relax_smem(const SmemState& st, uint32_t* nxt, int w, uint32_t nmE,
-                                          int* bad) {
-  if ((unsigned)w >= (unsigned)st.n) { *bad = 1; return 0; }
-  if (w < st.s) {
-    const uint32_t wE = st.base + 1u + (uint32_t)w;   // encoded value of label == w
-    if (st.fill_first && st.lab[w] < wE) return 0;   // already a fill: proposal stays w
-    const uint32_t old = atomicMin(&st.lab[w], nmE);
+template <>
+struct LabOps<uint16_t> {
+  static constexpr uint32_t MAXV = 0xFFFFu;
+  // 16-bit atomic minimum by compare-and-swap; returns the previous value
+  static __device__ __forceinline__ uint32_t amin(uint16_t* p, uint32_t v) {
+    unsigned short old = *(volatile unsigned short*)p;
+    while (v < old) {
+      const unsigned short prev = atomicCAS((unsigned short*)p, old, (unsigned short)v);
+      if (prev == old) break;
+      old = prev;
+    }
+    return old;
+  }
+};
+
+template <typename LabT>
+struct Src {
+  LabT* lab;
+  uint32_t* ub;
+  uint32_t* Dn;      // dedup bitmap of the list being built
+  LabT* Ln;          // list being built (shared part)
+  int32_t* Sn;       // list being built (spilled part)
+  int* qn;           // its length counter
+  uint32_t base;
+  int32_t s, n, cap, fill_first;
+};
+
+// Decide edge (f -> w) with encoded proposal nmE.  Returns 1 if w must be
+// appended to the next frontier (its dedup bit was set here).
+template <typename LabT>
+__device__ __forceinline__ int relax(const Src<LabT>& c, int w, uint32_t nmE, int* bad) {
+  if ((unsigned)w >= (unsigned)c.n) { *bad = 1; return 0; }
+  if (w < c.s) {
+    const uint32_t wE = c.base + 1u + (uint32_t)w;   // encoded value of maxId == w
+    if (c.fill_first && (uint32_t)c.lab[w] < wE) return 0;  // already a fill: proposal stays w
+    const uint32_t old = LabOps<LabT>::amin(&c.lab[w], nmE);
     if (nmE < old && old > wE) {
       const uint32_t bit = 1u << (w & 31);
-      if (!(nxt[w >> 5] & bit)) atomicOr(&nxt[w >> 5], bit);
-      return 1;
+      if (c.Dn[w >> 5] & bit) return 0;
+      return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
     }
-  } else if (w > st.s) {
+  } else if (w > c.s) {
     const uint32_t bit = 1u << (w & 31);
-    if (!(st.ub[w >> 5] & bit)) atomicOr(&st.ub[w >> 5], bit);
+    if (!(c.ub[w >> 5] & bit)) atomicOr(&c.ub[w >> 5], bit);
   }
   return 0;
 }
 
+// Append w (if enq) with one shared atomic per warp; all 32 lanes call this.
+template <typename LabT>
+__device__ __forceinline__ void append(const Src<LabT>& c, int enq, int w, int lane) {
+  const unsigned m = __ballot_sync(FULL, enq);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(c.qn, __popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (enq) {
+    const int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < c.cap) c.Ln[pos] = (LabT)w;
+    else c.Sn[pos - c.cap] = w;
+  }
+}
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 }  // namespace
 
-size_t trav_smem_bytes(int32_t n, int32_t S) {
+template <typename LabT>
+size_t trav_smem_bytes_t(int32_t n, int32_t S, int32_t cap) {
   const size_t SW = ((size_t)S + 31) / 32, NW = ((size_t)n + 31) / 32;
-  return 4 * ((size_t)S + 2 * SW + NW);
+  return align16(sizeof(LabT) * (size_t)S) + 4 * (2 * SW + NW) + align16(2 * sizeof(LabT) * (size_t)cap);
 }
 
-int32_t trav_smem_max_S(int32_t n, size_t smem_limit) {
-  const size_t NW = ((size_t)n + 31) / 32;
-  if (4 * NW + 64 >= smem_limit) return 0;
-  size_t S = (smem_limit - 4 * NW - 16) * 32 / (4 * 32 + 8);  // 4 bytes label + 2 frontier bits
-  S &= ~(size_t)31;
-  while (S > 0 && trav_smem_bytes(n, (int32_t)S) > smem_limit) S -= 32;
-  if (S > (size_t)n) S = (size_t)n;
-  return (int32_t)S;
+size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
+  return label16 ? trav_smem_bytes_t<uint16_t>(n, S, cap) : trav_smem_bytes_t<uint32_t>(n, S, cap);
 }
 
+template <typename LabT>
 __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
-  extern __shared__ uint32_t sm[];
-  const int n = a.n, S = a.S;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = a.n, S = a.S, CAP = a.list_cap;
   const int SW = (S + 31) >> 5, NW = (n + 31) >> 5;
-  uint32_t* lab = sm;
-  uint32_t* fA = lab + S;
-  uint32_t* fB = fA + SW;
-  uint32_t* ub = fB + SW;
+  LabT* lab = (LabT*)smraw;
+  uint32_t* D0 = (uint32_t*)(smraw + align16(sizeof(LabT) * (size_t)S));
+  uint32_t* D1 = D0 + SW;
+  uint32_t* ub = D1 + SW;
+  LabT* L0 = (LabT*)(ub + NW);
+  LabT* L1 = L0 + CAP;
+  int32_t* S0 = a.spill + (size_t)blockIdx.x * 2 * (size_t)a.spill_cap;
+  int32_t* S1 = S0 + a.spill_cap;
 
   __shared__ int s_src, s_diag;
+  __shared__ int s_q[3];
   __shared__ int s_wcL[32], s_wcU[32];
   __shared__ long long s_off;
   __shared__ int s_nL;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = blockDim.x, nwarps = nthr >> 5;
+  const unsigned lt = (1u << lane) - 1u;
 
-  for (int i = tid; i < S; i += nthr) lab[i] = 0xFFFFFFFFu;
-  for (int i = tid; i < SW; i += nthr) { fA[i] = 0u; fB[i] = 0u; }
+  for (int i = tid; i < S; i += nthr) lab[i] = (LabT)LabOps<LabT>::MAXV;
+  for (int i = tid; i < SW; i += nthr) { D0[i] = 0u; D1[i] = 0u; }
   for (int i = tid; i < NW; i += nthr) ub[i] = 0u;
 
-  const uint32_t span = (uint32_t)n + 2u;
-  uint32_t base = 0xFFFFFFFFu - span;
-  bool first = true;
+  // window base of the previous source; MAXV stands for the fill value
+  uint32_t base = LabOps<LabT>::MAXV;
   unsigned long long n_exp = 0, n_edge = 0;
   int bad = 0;
 
@@ -137,33 +175,35 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       const int k = atomicAdd(&a.ctr->work_smem, 1);
       s_src = (k < a.nsrc && !input_error(a.ctr)) ? a.order[k] : -1;
       s_diag = 0;
+      s_q[0] = s_q[1] = s_q[2] = 0;
     }
     __syncthreads();
     const int s = s_src;
     if (s < 0) break;
 
-    // next maxId window (Section 4); refill lab[] only when the range is used up
-    if (!first) {
-      if (base >= span) {
-        base -= span;
-      } else {
-        for (int i = tid; i < S; i += nthr) lab[i] = 0xFFFFFFFFu;
-        base = 0xFFFFFFFFu - span;
-        __syncthreads();
-      }
+    // maxId window of this source: encoded values base+1+l for l in [-1, s),
+    // strictly below every value an earlier source left behind
+    const uint32_t span = (uint32_t)s + 1u;
+    if (base >= span) {
+      base -= span;
+    } else {
+      for (int i = tid; i < S; i += nthr) lab[i] = (LabT)LabOps<LabT>::MAXV;
+      base = LabOps<LabT>::MAXV - span;
+      __syncthreads();
     }
-    first = false;
 
-    SmemState st{lab, ub, base, s, n, a.fill_first};
-
-    // seed: neighbours of s; those below s start the frontier with maxId -1
-    const int rb = a.rowptr[s], re = a.rowptr[s + 1];
+    // seed: neighbours of s; those below s form frontier 0 with maxId -1
+    const int rb = __ldg(a.rowptr + s), re = __ldg(a.rowptr + s + 1);
     for (int e = rb + tid; e < re; e += nthr) {
-      const int w = a.colidx[e];
+      const int w = __ldg(a.colidx + e);
       if ((unsigned)w >= (unsigned)n) { bad = 1; continue; }
       if (w < s) {
-        lab[w] = base;  // encoded -1
-        atomicOr(&fA[w >> 5], 1u << (w & 31));
+        lab[w] = (LabT)base;  // encoded -1
+        const uint32_t bit = 1u << (w & 31);
+        if (!(atomicOr(&D0[w >> 5], bit) & bit)) {  // once per vertex: the list holds < s entries
+          const int pos = atomicAdd(&s_q[0], 1);
+          if (pos < CAP) L0[pos] = (LabT)w; else S0[pos - CAP] = w;
+        }
       } else if (w > s) {
         atomicOr(&ub[w >> 5], 1u << (w & 31));
       } else {
@@ -172,74 +212,72 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     }
     __syncthreads();
 
-    uint32_t* cur = fA;
-    uint32_t* nxt = fB;
-    const int SWs = (s + 31) >> 5;
     // After k levels every maxId is at most the best value over paths of <= k
     // hops (each changed vertex is expanded again); simple paths through
     // vertices below s have at most s hops, so level s+2 changes nothing.
-    const long long cap = (long long)s + 3;
-    long long level = 0;
-    for (;;) {
-      int any = 0;
-      for (int b = warp * 32; b < SWs; b += nwarps * 32) {
-        const int wi = b + lane;
-        uint32_t word = 0u;
-        if (wi < SWs) {
-          word = cur[wi];
-          if (word) cur[wi] = 0u;
+    const int cap_lv = s + 3;
+    int qc = s_q[0];
+    for (int L = 1; qc > 0; L++) {
+      const int cb = (L - 1) & 1, nb = L & 1;
+      LabT* Lc = cb ? L1 : L0;
+      int32_t* Sc = cb ? S1 : S0;
+      uint32_t* Dc = cb ? D1 : D0;
+      Src<LabT> c{lab, ub, nb ? D1 : D0, nb ? L1 : L0, nb ? S1 : S0, &s_q[L % 3], base, s, n, CAP,
+                  a.fill_first};
+      if (tid == 0) s_q[(L + 1) % 3] = 0;
+      for (int r0 = warp * 32; r0 < qc; r0 += nthr) {
+        const int r = r0 + lane;
+        int v = -1, eb = 0, ee = 0;
+        uint32_t nmE = 0u;
+        if (r < qc) {
+          v = r < CAP ? (int)Lc[r] : Sc[r - CAP];
+          atomicAnd(&Dc[v >> 5], ~(1u << (v & 31)));  // v leaves the current list
+          eb = __ldg(a.rowptr + v);
+          ee = __ldg(a.rowptr + v + 1);
+          const uint32_t lv = (uint32_t)lab[v];
+          const uint32_t vE = base + 1u + (uint32_t)v;
+          nmE = lv > vE ? lv : vE;  // encoded max(maxId(v), v)
+          n_exp++;
+          n_edge += (unsigned long long)(ee - eb);
         }
-        const int cnt = __popc(word);
-        const int incl = warp_incl_scan(cnt, lane);
-        const int total = __shfl_sync(FULL, incl, 31);
-        for (int r0 = 0; r0 < total; r0 += 32) {
-          const int rank = r0 + lane;
-          int sl = 0;  // number of lanes whose inclusive count is <= rank
+        const int deg = (v >= 0 && ee - eb <= BIG_DEG) ? ee - eb : 0;
+        const int maxdeg = __reduce_max_sync(FULL, deg);
+        for (int k0 = 0; k0 < maxdeg; k0 += BATCH) {
+          int wv[BATCH];  // independent loads first, then the relaxations
 #pragma unroll
-          for (int bb = 16; bb >= 1; bb >>= 1) {
-            const int t = __shfl_sync(FULL, incl, sl + bb - 1);
-            if (t <= rank) sl += bb;
+          for (int q = 0; q < BATCH; q++) wv[q] = (k0 + q < deg) ? __ldg(a.colidx + eb + k0 + q) : 0;
+#pragma unroll
+          for (int q = 0; q < BATCH; q++) {
+            const int enq = (k0 + q < deg) ? relax(c, wv[q], nmE, &bad) : 0;
+            append(c, enq, wv[q], lane);
           }
-          const int slc = sl < 31 ? sl : 31;
-          const uint32_t wsrc = __shfl_sync(FULL, word, slc);
-          const int exsrc = __shfl_sync(FULL, incl, slc) - __popc(wsrc);
-          int v = -1;
-          if (rank < total) v = ((b + slc) << 5) + nth_set_bit(wsrc, rank - exsrc);
-
-          int eb = 0, ee = 0;
-          uint32_t nmE = 0u;
-          if (v >= 0) {
-            eb = a.rowptr[v];
-            ee = a.rowptr[v + 1];
-            const uint32_t lv = lab[v];
-            const uint32_t vE = base + 1u + (uint32_t)v;
-            nmE = lv > vE ? lv : vE;  // encoded max(maxId(v), v)
-            n_exp++;
-            if (ee - eb <= BIG_DEG) {
-              n_edge += (unsigned long long)(ee - eb);
-              for (int e = eb; e < ee; e++) any |= relax_smem(st, nxt, a.colidx[e], nmE, &bad);
-            }
-          }
-          unsigned bigm = __ballot_sync(FULL, v >= 0 && (ee - eb) > BIG_DEG);
-          while (bigm) {
-            const int l = __ffs(bigm) - 1;
-            bigm &= bigm - 1;
-            const int beb = __shfl_sync(FULL, eb, l), bee = __shfl_sync(FULL, ee, l);
-            const uint32_t bnm = __shfl_sync(FULL, nmE, l);
-            if (lane == 0) n_edge += (unsigned long long)(bee - beb);
-            for (int e = beb + lane; e < bee; e += 32) any |= relax_smem(st, nxt, a.colidx[e], bnm, &bad);
+        }
+        unsigned bigm = __ballot_sync(FULL, v >= 0 && (ee - eb) > BIG_DEG);
+        while (bigm) {  // long rows: the whole warp walks one row
+          const int l = __ffs(bigm) - 1;
+          bigm &= bigm - 1;
+          const int beb = __shfl_sync(FULL, eb, l), bee = __shfl_sync(FULL, ee, l);
+          const uint32_t bnm = __shfl_sync(FULL, nmE, l);
+          for (int e0 = beb; e0 < bee; e0 += 32) {
+            const int e = e0 + lane;
+            const int w = e < bee ? __ldg(a.colidx + e) : 0;
+            const int enq = e < bee ? relax(c, w, bnm, &bad) : 0;
+            append(c, enq, w, lane);
           }
         }
       }
-      level++;
-      any = __syncthreads_or(any);
-      uint32_t* t = cur;
-      cur = nxt;
-      nxt = t;
-      if (!any) break;
-      if (level >= cap) {
+      __syncthreads();
+      qc = s_q[L % 3];
+      if (qc > 0 && L >= cap_lv) {
+        // never expected: drop the frontier (clearing its dedup bits) and flag it
+        LabT* Ln = nb ? L1 : L0;
+        int32_t* Sn = nb ? S1 : S0;
+        uint32_t* Dn = nb ? D1 : D0;
+        for (int r = tid; r < qc; r += nthr) {
+          const int v = r < CAP ? (int)Ln[r] : Sn[r - CAP];
+          atomicAnd(&Dn[v >> 5], ~(1u << (v & 31)));
+        }
         if (tid == 0) atomicOr(&a.ctr->err, ERR_NOCONV);
-        for (int i = tid; i < SWs; i += nthr) cur[i] = 0u;
         __syncthreads();
         break;
       }
@@ -251,7 +289,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     int cL = 0;
     for (int i0 = loL; i0 < hiL; i0 += 32) {
       const int i = i0 + lane;
-      const bool f = i < hiL && lab[i] < base + 1u + (uint32_t)i;
+      const bool f = i < hiL && (uint32_t)lab[i] < base + 1u + (uint32_t)i;
       cL += __popc(__ballot_sync(FULL, f));
     }
     const int ws = (s + 1) >> 5;  // first word that can hold a column > s
@@ -291,9 +329,9 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       int pos = s_wcL[warp];
       for (int i0 = loL; i0 < hiL; i0 += 32) {
         const int i = i0 + lane;
-        const bool f = i < hiL && lab[i] < base + 1u + (uint32_t)i;
+        const bool f = i < hiL && (uint32_t)lab[i] < base + 1u + (uint32_t)i;
         const unsigned m = __ballot_sync(FULL, f);
-        if (f) a.pool[off + pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+        if (f) a.pool[off + pos + __popc(m & lt)] = (uint32_t)i;
         pos += __popc(m);
       }
     }
@@ -318,9 +356,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     }
   }
 
-  if (bad) {
-    atomicOr(&a.ctr->err, ERR_COL_RANGE);
-  }
+  if (bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
   if (a.collect_stats) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -334,36 +370,54 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   }
 }
 
-cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, cudaStream_t st) {
-  const size_t bytes = trav_smem_bytes(a.n, a.S);
-  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
-  if (e != cudaSuccess) return e;
-  trav_smem_kernel<<<grid, block, bytes, st>>>(a);
+template <typename LabT>
+static int32_t max_S_t(int32_t n, size_t limit, int32_t min_cap) {
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {  // largest S whose layout (with a list of min_cap entries) fits
+    const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) / 2);
+    const int32_t cap = mid < min_cap ? mid : min_cap;
+    if (trav_smem_bytes_t<LabT>(n, mid, cap) <= limit) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16) {
+  return label16 ? max_S_t<uint16_t>(n, smem_limit, 1024) : max_S_t<uint32_t>(n, smem_limit, 1024);
+}
+
+cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st) {
+  const size_t bytes = trav_smem_bytes(a.n, a.S, a.list_cap, label16);
+  if (label16) {
+    cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    trav_smem_kernel<uint16_t><<<grid, block, bytes, st>>>(a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    trav_smem_kernel<uint32_t><<<grid, block, bytes, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
-}  // namespace gsofa
-
-namespace gsofa {
-
 int trav_smem_static_bytes() {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, trav_smem_kernel) != cudaSuccess) {
+  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t>) != cudaSuccess) {
     cudaGetLastError();
     return 1024;
   }
   return (int)fa.sharedSizeBytes;
 }
 
-int trav_smem_occupancy(int block, size_t dyn_bytes) {
-  if (cudaFuncSetAttribute(trav_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes) !=
-      cudaSuccess) {
+int trav_smem_occupancy(int block, size_t dyn_bytes, int label16) {
+  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t> : (const void*)trav_smem_kernel<uint32_t>;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trav_smem_kernel, block, dyn_bytes) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, dyn_bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
