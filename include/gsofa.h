@@ -131,6 +131,30 @@ int gsofa_batch(int32_t count, const int32_t *n, const int32_t *const *d_rowptr,
                 const int32_t *const *d_colidx, const gsofa_options *opt, void *stream,
                 gsofa_result *outs);
 
+/*
+ * gsofa_row_counts_noalloc - per-row sizes of L and U and fill counts, without
+ * allocating any device memory.  The paper has no counterpart: this entry point
+ * is for callers that cannot allocate at the time they need the sizes (a
+ * solver that reserved the device's free memory for itself and hands out
+ * sub-buffers, a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device, a host that forbids allocation after start-up).
+ *   n                  order of A, 0 <= n <= GSOFA_NOALLOC_MAX_N (else GSOFA_E_INVAL)
+ *   d_rowptr, d_colidx device CSR of A (borrowed, validated on the device)
+ *   d_nnzL, d_nnzU     device int32[n]: nnz(L(i,:)) and nnz(U(i,:)) (diagonal included)
+ *   d_fill_count       device int32[n]: fill-ins of row i (as gsofa_result.fill_count)
+ *   stream             cudaStream_t; the call waits for its own work before returning
+ * Scratch: a fixed array of GSOFA_NOALLOC_SCRATCH_BYTES in device memory, held
+ * by every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address (once per device); make the
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (concurrent streams or host threads) race; serialise
+ * them.  No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+#define GSOFA_NOALLOC_MAX_N 65533
+#define GSOFA_NOALLOC_SCRATCH_BYTES (16u << 20)
+int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
+                             int32_t *d_nnzL, int32_t *d_nnzU, int32_t *d_fill_count, void *stream);
+
 /* Release every array of *res (device or host) and zero it.  NULL-safe.
  * Device arrays are freed stream-ordered on the stream of the call that made
  * them; the caller must not use them afterwards. */

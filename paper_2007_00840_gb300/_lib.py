@@ -17,6 +17,7 @@ GSOFA_E_TIMEOUT = -5
 GSOFA_E_BUSY = -6
 GSOFA_E_NOTFOUND = -7
 GSOFA_E_PENDING = -8
+GSOFA_NOALLOC_MAX_N = 65533
 
 
 class gsofa_options(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "gsofa_symbolic_device": (ctypes.c_int, [_I32, _P, _P, ctypes.POINTER(gsofa_options), _P,
                                              ctypes.POINTER(gsofa_result)]),
     "gsofa_batch": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(gsofa_options), _P, _P]),
+    "gsofa_row_counts_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P]),
     "gsofa_free": (None, [ctypes.POINTER(gsofa_result)]),
     "gsofa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gsofa_version": (ctypes.c_int, []),

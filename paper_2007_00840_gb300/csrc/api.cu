@@ -108,6 +108,8 @@ double timeout_seconds() {
   return 600.0;
 }
 
+}  // namespace
+
 // Bounded wait for all work queued on `st` (never an unbounded block).
 int wait_stream(cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -122,6 +124,8 @@ int wait_stream(cudaStream_t st) {
     if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
+
+namespace {
 
 Ctx* get_ctx(int* err) {
   int dev = 0;
@@ -243,9 +247,50 @@ struct Plan {
   int glob_grid = 0;
 };
 
-// Shared tier: largest S that fits one CTA, then the (block, CTAs per SM) pair
+}  // namespace
+
+// Shared tier launch shape for sources [0, S): the (block, CTAs per SM) pair
 // with the most resident threads (ties: more CTAs, i.e. more sources in
 // flight), then the largest frontier list that keeps that occupancy.
+int choose_smem_config(int sms, size_t limit, int32_t n, int32_t S, int label16, int threads_req, int* block,
+                       int* occ_out, int32_t* cap_out) {
+  (void)sms;
+  const int stat = trav_smem_static_bytes();
+  const int32_t min_cap = S < 1024 ? S : 1024;
+  const size_t per_sm = 233472;  // 228 KB of shared memory per SM
+  int best_block = 0, best_occ = 0;
+  const int blocks[4] = {1024, 512, 256, threads_req};
+  for (int bi = 0; bi < 4; bi++) {
+    const int b = blocks[bi];
+    if (b <= 0) continue;
+    if (threads_req > 0 && b != threads_req) continue;
+    const int occ = trav_smem_occupancy(b, trav_smem_bytes(n, S, min_cap, label16), label16);
+    if (occ < 1) continue;
+    if (occ * b > best_occ * best_block || (occ * b == best_occ * best_block && occ > best_occ)) {
+      best_block = b;
+      best_occ = occ;
+    }
+  }
+  if (best_block == 0) return GSOFA_E_CUDA;
+  size_t lim = per_sm / (size_t)best_occ;
+  lim = lim > (size_t)stat + 1024 + 64 ? lim - (size_t)stat - 1024 - 64 : 0;
+  if (lim > limit) lim = limit;
+  int32_t cap = S;
+  const size_t esz = label16 ? 2 : 4;
+  const size_t fixed = trav_smem_bytes(n, S, 0, label16);
+  if (fixed + 2 * esz * (size_t)cap > lim) cap = lim > fixed ? (int32_t)((lim - fixed) / (2 * esz)) : 0;
+  if (cap < S) cap &= ~31;
+  if (cap < min_cap) cap = min_cap;
+  while (cap > min_cap && trav_smem_occupancy(best_block, trav_smem_bytes(n, S, cap, label16), label16) < best_occ)
+    cap = (cap / 2 > min_cap) ? cap / 2 : min_cap;
+  *block = best_block;
+  *occ_out = best_occ;
+  *cap_out = cap;
+  return GSOFA_OK;
+}
+
+namespace {
+
 int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   const int stat = trav_smem_static_bytes();
   const int label16 = n <= 65533 ? 1 : 0;
@@ -258,41 +303,13 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   p->S = S;
   p->label16 = label16;
   if (S > 0) {
-    const int32_t min_cap = S < 1024 ? S : 1024;
-    const size_t per_sm = 233472;  // 228 KB of shared memory per SM
-    int best_block = 0, best_occ = 0;
-    const int blocks[3] = {1024, 512, 256};
-    for (int bi = 0; bi < 3; bi++) {
-      const int b = blocks[bi];
-      if (o.threads_per_source > 0 && b != o.threads_per_source) continue;
-      const int occ = trav_smem_occupancy(b, trav_smem_bytes(n, S, min_cap, label16), label16);
-      if (occ < 1) continue;
-      if (occ * b > best_occ * best_block || (occ * b == best_occ * best_block && occ > best_occ)) {
-        best_block = b;
-        best_occ = occ;
-      }
-    }
-    if (o.threads_per_source > 0 && best_block == 0) {
-      const int b = o.threads_per_source;
-      const int occ = trav_smem_occupancy(b, trav_smem_bytes(n, S, min_cap, label16), label16);
-      if (occ >= 1) { best_block = b; best_occ = occ; }
-    }
-    if (best_block == 0) return GSOFA_E_CUDA;
-    // largest list capacity that keeps best_occ CTAs per SM
-    size_t lim = per_sm / (size_t)best_occ;
-    lim = lim > (size_t)stat + 1024 + 64 ? lim - (size_t)stat - 1024 - 64 : 0;
-    if (lim > limit) lim = limit;
-    int32_t cap = S;
-    const size_t esz = label16 ? 2 : 4;
-    const size_t fixed = trav_smem_bytes(n, S, 0, label16);
-    if (fixed + 2 * esz * (size_t)cap > lim) cap = lim > fixed ? (int32_t)((lim - fixed) / (2 * esz)) : 0;
-    cap &= ~31;
-    if (cap < min_cap) cap = min_cap;
-    while (cap > min_cap && trav_smem_occupancy(best_block, trav_smem_bytes(n, S, cap, label16), label16) < best_occ)
-      cap = (cap / 2 > min_cap) ? cap / 2 : min_cap;
+    int block = 0, occ = 0;
+    int32_t cap = 0;
+    const int rc = choose_smem_config(c->sms, limit, n, S, label16, o.threads_per_source, &block, &occ, &cap);
+    if (rc) return rc;
     p->list_cap = cap;
-    p->smem_block = best_block;
-    p->smem_grid = c->sms * best_occ;
+    p->smem_block = block;
+    p->smem_grid = c->sms * occ;
   }
   if (S < n) {
     int block = o.threads_per_source > 0 ? o.threads_per_source : 512;

@@ -44,7 +44,7 @@ struct TravArgs {
   int32_t n;
   const int32_t* __restrict__ rowptr;
   const int32_t* __restrict__ colidx;
-  const int32_t* __restrict__ order;  // source rows to process, in order of issue
+  const int32_t* __restrict__ order;  // source rows to process, in order of issue (null: nsrc-1 .. 0)
   int32_t nsrc;
   int32_t S;                          // shared tier: label capacity (all sources < S)
   int32_t list_cap;                   // shared tier: frontier list capacity in shared memory
@@ -59,6 +59,7 @@ struct TravArgs {
   DevCounters* ctr;
   int32_t fill_first;                 // optional "line 9.5" of Section 4
   int32_t collect_stats;
+  int32_t counts_only;                // 1: write per-row counts only (no pool, no row_off)
   // global tier: per-slot working arrays (slot = CTA index)
   uint32_t* g_lab;                    // slots x n (epoch-encoded maxId)
   int32_t* g_queue;                   // slots x 2n (current / next frontier)
@@ -97,5 +98,10 @@ cudaError_t launch_scatter_starts(int32_t n, const int32_t* flags, const int64_t
 cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t st);
 cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
 cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
+
+// host helpers (api.cu)
+int wait_stream(cudaStream_t st);  // bounded wait; GSOFA_OK / GSOFA_E_TIMEOUT / GSOFA_E_CUDA
+int choose_smem_config(int sms, size_t limit, int32_t n, int32_t S, int label16, int threads_req, int* block,
+                       int* occ, int32_t* cap);
 
 }  // namespace gsofa

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     __syncthreads();
     if (tid == 0) {
       const int k = atomicAdd(&a.ctr->work_smem, 1);
-      s_src = (k < a.nsrc && !input_error(a.ctr)) ? a.order[k] : -1;
+      s_src = (k < a.nsrc && !input_error(a.ctr)) ? (a.order ? a.order[k] : a.nsrc - 1 - k) : -1;
       s_diag = 0;
       s_q[0] = s_q[1] = s_q[2] = 0;
     }
@@ -309,18 +309,22 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         const int y = s_wcU[w]; s_wcU[w] = tu; tu += y;
       }
       const int nL = tl, nU = tu + 1;
-      const unsigned long long off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
-      const bool ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
+      bool ok = false;
+      unsigned long long off = 0ull;
+      if (!a.counts_only) {
+        off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
+        ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
+        a.row_off[s] = ok ? (int64_t)off : -1;
+        if (ok) a.pool[off + nL] = (uint32_t)s;
+        else atomicOr(&a.ctr->err, ERR_OVERFLOW);
+      }
       s_off = ok ? (long long)off : -1LL;
       s_nL = nL;
-      a.row_off[s] = ok ? (int64_t)off : -1;
       a.row_nL[s] = nL;
       a.row_nU[s] = nU;
       a.fill_count[s] = nL + nU - ((re - rb) + (s_diag ? 0 : 1));
       atomicAdd(&a.ctr->total_L, (unsigned long long)nL);
       atomicAdd(&a.ctr->total_U, (unsigned long long)nU);
-      if (ok) a.pool[off + nL] = (uint32_t)s;
-      else atomicOr(&a.ctr->err, ERR_OVERFLOW);
     }
     __syncthreads();
     const long long off = s_off;
