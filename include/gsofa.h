@@ -62,7 +62,12 @@ typedef struct gsofa_options {
                                     (the optional "line 9.5" of Section 4); same result */
     int32_t collect_stats;       /* 1: record per-phase CUDA-event times and work counters */
     int32_t validate;            /* 0 or 1: check the CSR on the device first (default 1); 2: skip */
-    int32_t reserved[7];
+    int32_t autotune;            /* gsofa_batch: 1 = time candidate launch shapes once per batch shape
+                                    (block size, frontier list capacity, work items per fetch) and keep
+                                    the fastest; 0 = heuristic shape */
+    int32_t work_chunk;          /* work items a CTA takes per fetch (default 1) */
+    int32_t list_capacity;       /* frontier list entries kept in shared memory (default: as many as fit) */
+    int32_t reserved[4];
 } gsofa_options;
 
 /* Per-call statistics (filled when options.collect_stats == 1). */
@@ -121,11 +126,18 @@ int gsofa_symbolic_device(int32_t n, const int32_t *d_rowptr, const int32_t *d_c
                           const gsofa_options *opt, void *stream, gsofa_result *out);
 
 /*
- * gsofa_batch - many independent matrices in one pass (spec batching of
- * the Section 4/5 method).  Matrix k is (n[k], d_rowptr[k], d_colidx[k]) on the
- * device.  The sources of all matrices are scheduled together in persistent
- * traversal kernels (largest source first); outs[k] receives matrix k's
- * device result (release each with gsofa_free()).
+ * gsofa_batch - many independent matrices in one pass: the Section 4 traversal
+ * and Section 5 supernode detection of every matrix, with the source rows of
+ * all matrices scheduled together.  Matrix k is (n[k], d_rowptr[k],
+ * d_colidx[k]) on the current device (borrowed).  Matrices whose maxId arrays
+ * fit in shared memory run in ONE persistent traversal launch whose work items
+ * are (matrix, source row) pairs, largest source row first across the batch;
+ * the launch sequence up to the size read-back is captured once per batch
+ * signature (matrix count, orders, input pointers, options) into a CUDA graph
+ * and replayed on later calls with the same signature.  Larger matrices run
+ * one after another through the single-matrix path.  outs[k] receives matrix
+ * k's device result; batch members share one allocation that is released when
+ * the last of them is passed to gsofa_free().  On error every out is zeroed.
  */
 int gsofa_batch(int32_t count, const int32_t *n, const int32_t *const *d_rowptr,
                 const int32_t *const *d_colidx, const gsofa_options *opt, void *stream,

@@ -30,7 +30,10 @@ class gsofa_options(ctypes.Structure):
         ("fill_first", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32),
         ("validate", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("autotune", ctypes.c_int32),
+        ("work_chunk", ctypes.c_int32),
+        ("list_capacity", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

@@ -6,7 +6,10 @@
 // on chip, global tier for the rest) -> T3 supernode flags (Section 5) ->
 // one read-back of the sizes -> prefix sums, row compaction into L/U CSR and
 // the supernode list.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <unordered_map>
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
@@ -47,12 +50,21 @@ struct Ctx {
 std::mutex g_ctx_mu;
 Ctx* g_ctx[128] = {nullptr};
 
+// Device allocations shared by the results of one batch; freed with the last.
+struct SharedBlock {
+  std::atomic<int> refs{0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<void*> ptrs;
+};
+
 struct Priv {
   cudaStream_t stream = nullptr;
   int device = 0;
   cudaMemPool_t mpool = nullptr;
   void* host_block = nullptr;   // host results: one pinned block holding every array
   size_t host_cap = 0;
+  SharedBlock* shared = nullptr;  // batch results: arrays point into this block
 };
 
 // Pinned host blocks are expensive to create (page locking), so results of the
@@ -307,6 +319,8 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     int32_t cap = 0;
     const int rc = choose_smem_config(c->sms, limit, n, S, label16, o.threads_per_source, &block, &occ, &cap);
     if (rc) return rc;
+    if (o.list_capacity > 0 && o.list_capacity < cap) cap = o.list_capacity < 32 ? 32 : o.list_capacity;
+    if (cap > S) cap = S;
     p->list_cap = cap;
     p->smem_block = block;
     p->smem_grid = c->sms * occ;
@@ -335,6 +349,10 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->smem_max_source = in->smem_max_source;
   o->max_concurrent = in->max_concurrent;
   o->mem_budget_bytes = in->mem_budget_bytes;
+  if (in->work_chunk < 0 || in->list_capacity < 0) return GSOFA_E_INVAL;
+  o->autotune = in->autotune ? 1 : 0;
+  o->work_chunk = in->work_chunk;
+  o->list_capacity = in->list_capacity;
   o->fill_first = in->fill_first ? 1 : 0;
   o->collect_stats = in->collect_stats ? 1 : 0;
   o->validate = in->validate;
@@ -479,6 +497,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.list_cap = plan.list_cap;
       a.spill = spill;
       a.spill_cap = spill_cap;
+      a.chunk = o.work_chunk > 0 ? o.work_chunk : 1;
       LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, plan.label16, st));
     }
     ev.rec(4, st);
@@ -583,6 +602,524 @@ fail:
 #undef CK
 }
 
+
+// ------------------------------------------------------------------ batches
+// Launch shape of the shared-memory traversal for one batch shape.
+struct LaunchShape {
+  int block = 512;
+  int occ = 1;
+  int32_t list_cap = 1024;
+  int work_chunk = 1;
+};
+
+// Workspace and captured graph of one batch signature.
+struct BatchPlan {
+  uint64_t sig = 0;
+  uint64_t last_use = 0;
+  int32_t B = 0;                    // matrices in the batched launch
+  std::vector<int32_t> members;     // their indices in the caller's arrays
+  std::vector<int64_t> row_base;
+  int32_t n_max = 0;
+  int64_t N = 0, chunks = 0;
+  int label16 = 1;
+  LaunchShape shape;
+  MatDesc* d_mats = nullptr;
+  int32_t* d_item_start = nullptr;
+  int32_t* d_mat_order = nullptr;
+  unsigned char* d_ctr = nullptr;   // DevCounters | per matrix [nL, nU] | per matrix n_super
+  unsigned char* h_ctr = nullptr;   // pinned copy of d_ctr
+  size_t ctr_bytes = 0;
+  int64_t* row_off = nullptr;
+  int32_t *row_nL = nullptr, *row_nU = nullptr, *flags = nullptr, *fill = nullptr;
+  uint32_t* pool = nullptr;
+  long long pool_cap = 0;
+  int32_t* spill = nullptr;
+  int64_t spill_cap = 0;
+  int64_t spill_alloc = 0;
+  int grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+
+  DevCounters* ctr() const { return (DevCounters*)d_ctr; }
+  unsigned long long* mat_tot() const { return (unsigned long long*)(d_ctr + 256); }
+  int32_t* mat_nsuper() const { return (int32_t*)(d_ctr + 256 + 16 * (size_t)B); }
+  const DevCounters* hctr() const { return (const DevCounters*)h_ctr; }
+  const unsigned long long* h_tot() const { return (const unsigned long long*)(h_ctr + 256); }
+  const int32_t* h_nsuper() const { return (const int32_t*)(h_ctr + 256 + 16 * (size_t)B); }
+};
+
+void free_plan(BatchPlan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  cudaFree(p->d_mats);
+  cudaFree(p->d_item_start);
+  cudaFree(p->d_mat_order);
+  cudaFree(p->d_ctr);
+  cudaFree(p->row_off);
+  cudaFree(p->row_nL);
+  cudaFree(p->row_nU);
+  cudaFree(p->flags);
+  cudaFree(p->fill);
+  cudaFree(p->pool);
+  cudaFree(p->spill);
+  if (p->h_ctr) cudaFreeHost(p->h_ctr);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  delete p;
+}
+
+struct BatchCache {
+  std::mutex mu;
+  std::unordered_map<uint64_t, BatchPlan*> plans;
+  uint64_t clock = 0;
+  std::map<uint64_t, LaunchShape> tuned;  // shape bucket -> fastest launch shape
+  bool file_loaded = false;
+};
+BatchCache g_batch[128];
+
+uint64_t mix64(uint64_t h, uint64_t v) {
+  h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h * 0xBF58476D1CE4E5B9ull;
+}
+
+uint64_t bucket_key(int32_t n_max, int64_t N, int label16) {
+  int a = 0, b = 0;
+  while ((1LL << a) < n_max) a++;
+  while ((1LL << b) < N) b++;
+  return ((uint64_t)a << 32) | ((uint64_t)b << 8) | (uint64_t)label16;
+}
+
+// Tuning results persist in the file named by GSOFA_TUNE_FILE (optional).
+void load_tune_file(BatchCache& bc) {
+  if (bc.file_loaded) return;
+  bc.file_loaded = true;
+  const char* f = std::getenv("GSOFA_TUNE_FILE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  unsigned long long key;
+  int block, occ, cap, chunk;
+  while (std::fscanf(fp, "%llx %d %d %d %d", &key, &block, &occ, &cap, &chunk) == 5) {
+    LaunchShape sh;
+    sh.block = block; sh.occ = occ; sh.list_cap = cap; sh.work_chunk = chunk;
+    bc.tuned[key] = sh;
+  }
+  std::fclose(fp);
+}
+
+void save_tune_entry(uint64_t key, const LaunchShape& sh) {
+  const char* f = std::getenv("GSOFA_TUNE_FILE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%llx %d %d %d %d\n", (unsigned long long)key, sh.block, sh.occ, sh.list_cap, sh.work_chunk);
+  std::fclose(fp);
+}
+
+// Launch shapes worth timing for a batch whose largest order is n_max.
+std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, size_t limit) {
+  std::vector<LaunchShape> out;
+  const int blocks[3] = {256, 512, 1024};
+  for (int b : blocks) {
+    int block = 0, occ = 0;
+    int32_t cap = 0;
+    if (choose_smem_config(c->sms, limit, n_max, n_max, label16, b, &block, &occ, &cap) != GSOFA_OK) continue;
+    const int32_t caps[2] = {cap, n_max < 1024 ? n_max : 1024};
+    for (int ci = 0; ci < 2; ci++) {
+      if (ci == 1 && caps[1] >= cap) continue;
+      for (int chunk : {1, 4}) {
+        LaunchShape sh;
+        sh.block = block; sh.occ = occ; sh.list_cap = caps[ci]; sh.work_chunk = chunk;
+        out.push_back(sh);
+      }
+    }
+  }
+  return out;
+}
+
+// Enqueue the first phase (counters, validation, traversal, supernodes, size read-back).
+cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStream_t st, cudaEvent_t t0,
+                           cudaEvent_t t1) {
+  cudaError_t e;
+  if ((e = launch_init_counters(p.ctr(), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(p.d_ctr + 256, 0, p.ctr_bytes - 256, st)) != cudaSuccess) return e;
+  if (o.validate != 2 && (e = launch_validate_batch(p.d_mats, p.B, p.N, p.ctr(), st)) != cudaSuccess) return e;
+  TravArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = p.n_max;
+  a.S = p.n_max;
+  a.nsrc = (int32_t)p.N;
+  a.list_cap = p.shape.list_cap;
+  a.spill = p.spill;
+  a.spill_cap = p.spill_cap;
+  a.pool = p.pool;
+  a.pool_cap = p.pool_cap;
+  a.row_off = p.row_off;
+  a.row_nL = p.row_nL;
+  a.row_nU = p.row_nU;
+  a.fill_count = p.fill;
+  a.ctr = p.ctr();
+  a.fill_first = o.fill_first;
+  a.collect_stats = o.collect_stats;
+  a.mats = p.d_mats;
+  a.item_start = p.d_item_start;
+  a.mat_order = p.d_mat_order;
+  a.nmats = p.B;
+  a.chunk = p.shape.work_chunk;
+  a.mat_tot = p.mat_tot();
+  if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
+  if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) return e;
+  if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
+  if ((e = launch_supernode_batch(p.d_mats, p.B, p.chunks, o.chunk_size, p.pool, p.row_off, p.row_nL, p.row_nU,
+                                  p.flags, p.mat_nsuper(), p.ctr(), st)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(p.h_ctr, p.d_ctr, p.ctr_bytes, cudaMemcpyDeviceToHost, st);
+}
+
+int set_shape(Ctx* c, BatchPlan* p, const LaunchShape& sh) {
+  p->shape = sh;
+  p->grid = c->sms * sh.occ;
+  // per CTA two overflow lists of (n_max - list capacity) entries
+  p->spill_cap = p->n_max > sh.list_cap ? (int64_t)p->n_max - sh.list_cap : 1;
+  const int64_t need = (int64_t)p->grid * 2 * p->spill_cap;
+  if (!p->spill || need > p->spill_alloc) {
+    cudaFree(p->spill);
+    p->spill = nullptr;
+    p->spill_alloc = 0;
+    if (cudaMalloc(&p->spill, sizeof(int32_t) * (size_t)need) != cudaSuccess) {
+      cudaGetLastError();
+      p->spill = nullptr;
+      return GSOFA_E_NOMEM;
+    }
+    p->spill_alloc = need;
+  }
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return GSOFA_OK;
+}
+
+int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
+               const int32_t* const* ci, const gsofa_options& o, uint64_t sig, BatchPlan** out) {
+  BatchPlan* p = new BatchPlan();
+  p->sig = sig;
+  p->members = members;
+  p->B = (int32_t)members.size();
+  std::vector<MatDesc> mats(p->B);
+  int64_t rbase = 0, cbase = 0;
+  for (int32_t k = 0; k < p->B; k++) {
+    const int32_t nk = n[members[k]];
+    mats[k].rowptr = rp[members[k]];
+    mats[k].colidx = ci[members[k]];
+    mats[k].n = nk;
+    mats[k].row_base = rbase;
+    mats[k].chunk_base = cbase;
+    p->row_base.push_back(rbase);
+    rbase += nk;
+    cbase += (nk + o.chunk_size - 1) / o.chunk_size;
+    if (nk > p->n_max) p->n_max = nk;
+  }
+  p->N = rbase;
+  p->chunks = cbase;
+  p->label16 = p->n_max <= 65533 ? 1 : 0;
+  // work order: source index descending, then matrices by decreasing order
+  std::vector<int32_t> order(p->B);
+  for (int32_t k = 0; k < p->B; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return mats[x].n > mats[y].n; });
+  std::vector<int32_t> item_start(p->n_max > 0 ? p->n_max : 1, 0);
+  {
+    // cnt(s) = #{m : n_m > s}; item_start[s] = sum_{s' > s} cnt(s')
+    std::vector<int32_t> cnt(p->n_max + 1, 0);
+    for (int32_t k = 0; k < p->B; k++) cnt[mats[k].n]++;  // count by n, then suffix sums
+    int32_t above = 0;
+    std::vector<int32_t> c_s(p->n_max, 0);
+    for (int32_t s = p->n_max - 1; s >= 0; s--) {
+      above += cnt[s + 1];
+      c_s[s] = above;  // matrices with n > s
+    }
+    int64_t acc = 0;
+    for (int32_t s = p->n_max - 1; s >= 0; s--) {
+      item_start[s] = (int32_t)acc;
+      acc += c_s[s];
+    }
+  }
+  p->ctr_bytes = 256 + 16 * (size_t)p->B + 4 * (size_t)p->B;
+  {
+    std::lock_guard<std::mutex> lk(c->hmu);
+    auto it = c->pool_hint.find(-(int32_t)(sig & 0x7FFFFFFF) - 1);
+    p->pool_cap = it != c->pool_hint.end() ? it->second : 64 * p->N + (1 << 20);
+  }
+  bool ok = cudaMalloc(&p->d_mats, sizeof(MatDesc) * (size_t)(p->B > 0 ? p->B : 1)) == cudaSuccess &&
+            cudaMalloc(&p->d_item_start, sizeof(int32_t) * item_start.size()) == cudaSuccess &&
+            cudaMalloc(&p->d_mat_order, sizeof(int32_t) * (size_t)(p->B > 0 ? p->B : 1)) == cudaSuccess &&
+            cudaMalloc(&p->d_ctr, p->ctr_bytes) == cudaSuccess &&
+            cudaMallocHost(&p->h_ctr, p->ctr_bytes) == cudaSuccess &&
+            cudaMalloc(&p->row_off, sizeof(int64_t) * (size_t)p->N) == cudaSuccess &&
+            cudaMalloc(&p->row_nL, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
+            cudaMalloc(&p->row_nU, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
+            cudaMalloc(&p->flags, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
+            cudaMalloc(&p->fill, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
+            cudaMalloc(&p->pool, sizeof(uint32_t) * (size_t)p->pool_cap) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_plan(p);
+    return GSOFA_E_NOMEM;
+  }
+  if (cudaMemcpy(p->d_mats, mats.data(), sizeof(MatDesc) * (size_t)p->B, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_item_start, item_start.data(), sizeof(int32_t) * item_start.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->d_mat_order, order.data(), sizeof(int32_t) * (size_t)p->B, cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    free_plan(p);
+    return GSOFA_E_CUDA;
+  }
+  *out = p;
+  return GSOFA_OK;
+}
+
+// Time every candidate launch shape once on this batch and keep the fastest.
+int autotune_plan(Ctx* c, BatchPlan* p, const gsofa_options& o, cudaStream_t st, size_t limit) {
+  std::vector<LaunchShape> cands = candidate_shapes(c, p->n_max, p->label16, limit);
+  if (cands.empty()) return GSOFA_E_CUDA;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  float best = 1e30f;
+  LaunchShape best_sh = cands[0];
+  for (const LaunchShape& sh : cands) {
+    int rc = set_shape(c, p, sh);
+    if (rc) { cudaEventDestroy(t0); cudaEventDestroy(t1); return rc; }
+    if (enqueue_phase1(*p, o, st, t0, t1) != cudaSuccess) { cudaEventDestroy(t0); cudaEventDestroy(t1); return GSOFA_E_CUDA; }
+    rc = wait_stream(st);
+    if (rc) { cudaEventDestroy(t0); cudaEventDestroy(t1); return rc; }
+    if (p->hctr()->err & (ERR_INPUT | ERR_NOCONV)) break;  // reported by the real run
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (ms < best) { best = ms; best_sh = sh; }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return set_shape(c, p, best_sh);
+}
+
+int capture_plan(BatchPlan* p, const gsofa_options& o) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return GSOFA_E_CUDA;
+  const cudaError_t e1 = enqueue_phase1(*p, o, p->cap_stream, nullptr, nullptr);
+  const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return GSOFA_E_CUDA;
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&p->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    cudaGetLastError();
+    p->gexec = nullptr;
+    return GSOFA_E_CUDA;
+  }
+  return GSOFA_OK;
+}
+
+// Batched path for the members that fit the shared-memory tier.
+int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
+                      const int32_t* const* ci, const gsofa_options& o, cudaStream_t st, gsofa_result* outs,
+                      int* launches) {
+  BatchCache& bc = g_batch[c->device];
+  uint64_t sig = 0x5EED;
+  for (int32_t k : members) {
+    sig = mix64(sig, (uint64_t)k);  // position in the caller's arrays
+    sig = mix64(sig, (uint64_t)n[k]);
+    sig = mix64(sig, (uint64_t)(uintptr_t)rp[k]);
+    sig = mix64(sig, (uint64_t)(uintptr_t)ci[k]);
+  }
+  sig = mix64(sig, ((uint64_t)o.chunk_size << 32) ^ ((uint64_t)o.fill_first << 8) ^ (uint64_t)o.validate);
+  sig = mix64(sig, ((uint64_t)o.work_chunk << 32) ^ ((uint64_t)o.list_capacity << 4) ^ (uint64_t)o.threads_per_source);
+  sig = mix64(sig, (uint64_t)o.collect_stats);
+  std::unique_lock<std::mutex> lk(bc.mu);  // one batch at a time per device uses a plan
+  load_tune_file(bc);
+  BatchPlan* p = nullptr;
+  auto it = bc.plans.find(sig);
+  if (it != bc.plans.end()) {
+    p = it->second;
+  } else {
+    int rc = build_plan(c, members, n, rp, ci, o, sig, &p);
+    if (rc) return rc;
+    const int stat = trav_smem_static_bytes();
+    const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
+    const uint64_t key = bucket_key(p->n_max, p->N, p->label16) ^ ((uint64_t)o.threads_per_source << 48);
+    auto tt = bc.tuned.find(key);
+    if (o.autotune && o.threads_per_source == 0 && o.list_capacity == 0 && o.work_chunk == 0 && tt == bc.tuned.end()) {
+      rc = autotune_plan(c, p, o, st, limit);
+      if (rc) { free_plan(p); return rc; }
+      bc.tuned[key] = p->shape;
+      save_tune_entry(key, p->shape);
+    } else {
+      LaunchShape sh;
+      if (tt != bc.tuned.end() && o.list_capacity == 0 && o.work_chunk == 0) {
+        sh = tt->second;
+      } else {
+        int32_t cap = 0;
+        rc = choose_smem_config(c->sms, limit, p->n_max, p->n_max, p->label16, o.threads_per_source, &sh.block,
+                                &sh.occ, &cap);
+        if (rc) { free_plan(p); return rc; }
+        if (o.list_capacity > 0 && o.list_capacity < cap) cap = o.list_capacity < 32 ? 32 : o.list_capacity;
+        sh.list_cap = cap;
+        sh.work_chunk = o.work_chunk > 0 ? o.work_chunk : 1;
+      }
+      rc = set_shape(c, p, sh);
+      if (rc) { free_plan(p); return rc; }
+    }
+    if (bc.plans.size() >= 8) {  // keep at most 8 plans: drop the least recently used
+      auto victim = bc.plans.begin();
+      for (auto jt = bc.plans.begin(); jt != bc.plans.end(); ++jt)
+        if (jt->second->last_use < victim->second->last_use) victim = jt;
+      cudaDeviceSynchronize();
+      free_plan(victim->second);
+      bc.plans.erase(victim);
+    }
+    bc.plans[sig] = p;
+  }
+  p->last_use = ++bc.clock;
+
+  for (int attempt = 0; attempt < 3; attempt++) {
+    if (!p->gexec && capture_plan(p, o) != GSOFA_OK) {
+      // graph capture unavailable: launch directly
+      if (enqueue_phase1(*p, o, st, nullptr, nullptr) != cudaSuccess) return GSOFA_E_CUDA;
+    } else if (cudaGraphLaunch(p->gexec, st) != cudaSuccess) {
+      return GSOFA_E_CUDA;
+    }
+    *launches += 4 + (o.validate != 2 ? 1 : 0);
+    int rc = wait_stream(st);
+    if (rc) return rc;
+    const DevCounters* h = p->hctr();
+    if (h->err & ERR_INPUT) return GSOFA_E_INVAL;
+    if (h->err & ERR_NOCONV) return GSOFA_E_NOCONVERGE;
+    if (!(h->err & ERR_OVERFLOW)) break;
+    // the row pool was too small; the totals are exact now
+    const long long need = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
+    cudaFree(p->pool);
+    p->pool = nullptr;
+    if (cudaMalloc(&p->pool, sizeof(uint32_t) * (size_t)need) != cudaSuccess) {
+      cudaGetLastError();
+      p->pool_cap = 0;
+      bc.plans.erase(p->sig);
+      free_plan(p);
+      return GSOFA_E_NOMEM;
+    }
+    p->pool_cap = need;
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    if (attempt == 2) return GSOFA_E_NOMEM;
+  }
+
+  // phase 2: exact outputs for every member in one shared allocation
+  const DevCounters* h = p->hctr();
+  const int64_t total_L = (int64_t)h->total_L, total_U = (int64_t)h->total_U;
+  const int64_t total_super = h->n_super;
+  SharedBlock* blk = new SharedBlock();
+  blk->stream = st;
+  blk->device = c->device;
+  int64_t *Lrp = nullptr, *Urp = nullptr, *GL = nullptr, *GU = nullptr, *P = nullptr;
+  int32_t *Lci = nullptr, *Uci = nullptr, *sup = nullptr, *fill = nullptr;
+  void* tmp = nullptr;
+  bool ok = palloc(c, &Lrp, (size_t)(p->N + p->B), st) == cudaSuccess &&
+            palloc(c, &Urp, (size_t)(p->N + p->B), st) == cudaSuccess &&
+            palloc(c, &Lci, (size_t)total_L, st) == cudaSuccess && palloc(c, &Uci, (size_t)total_U, st) == cudaSuccess &&
+            palloc(c, &sup, (size_t)(total_super + p->B), st) == cudaSuccess &&
+            palloc(c, &fill, (size_t)p->N, st) == cudaSuccess && palloc(c, &GL, (size_t)p->N + 1, st) == cudaSuccess &&
+            palloc(c, &GU, (size_t)p->N + 1, st) == cudaSuccess && palloc(c, &P, (size_t)p->N + 1, st) == cudaSuccess &&
+            cudaMallocFromPoolAsync(&tmp, scan_tmp_bytes_long(p->N), c->mpool, st) == cudaSuccess;
+  for (void* q : {(void*)Lrp, (void*)Urp, (void*)Lci, (void*)Uci, (void*)sup, (void*)fill})
+    if (q) blk->ptrs.push_back(q);
+  cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = launch_scan_i32_i64_long(p->row_nL, GL, p->N, tmp, st);
+  if (e == cudaSuccess) e = launch_scan_i32_i64_long(p->row_nU, GU, p->N, tmp, st);
+  if (e == cudaSuccess) e = launch_rebase_rowptr(p->d_mats, p->B, p->N, GL, Lrp, st);
+  if (e == cudaSuccess) e = launch_rebase_rowptr(p->d_mats, p->B, p->N, GU, Urp, st);
+  if (e == cudaSuccess) e = launch_compact_long(p->N, p->pool, p->row_off, p->row_nL, p->row_nU, GL, GU, Lci, Uci, st);
+  if (e == cudaSuccess) e = launch_scan_i32_i64_long(p->flags, P, p->N, tmp, st);
+  if (e == cudaSuccess) e = launch_scatter_starts_batch(p->d_mats, p->B, p->N, p->flags, P, sup, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fill, p->fill, sizeof(int32_t) * (size_t)p->N, cudaMemcpyDeviceToDevice, st);
+  *launches += 3 * 3 + 4;
+  pfree(GL, st);
+  pfree(GU, st);
+  pfree(P, st);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (void* q : blk->ptrs) cudaFreeAsync(q, st);
+    delete blk;
+    return ok ? GSOFA_E_CUDA : GSOFA_E_NOMEM;
+  }
+  // hand out views into the block (host-side prefix sums of the per-matrix totals)
+  const unsigned long long* tot = p->h_tot();
+  const int32_t* ns = p->h_nsuper();
+  int64_t offL = 0, offU = 0, offS = 0;
+  blk->refs.store(p->B);
+  for (int32_t k = 0; k < p->B; k++) {
+    gsofa_result* r = &outs[p->members[k]];
+    zero_result(r);
+    Priv* pv = new Priv();
+    pv->stream = st;
+    pv->device = c->device;
+    pv->shared = blk;
+    r->_priv = pv;
+    r->n = n[p->members[k]];
+    r->on_device = 1;
+    r->err_detail = -1;
+    r->nnz_L = (int64_t)tot[2 * k];
+    r->nnz_U = (int64_t)tot[2 * k + 1];
+    r->n_super = ns[k];
+    r->L_rowptr = Lrp + p->row_base[k] + k;
+    r->U_rowptr = Urp + p->row_base[k] + k;
+    r->L_colidx = Lci + offL;
+    r->U_colidx = Uci + offU;
+    r->fill_count = fill + p->row_base[k];
+    r->super_start = sup + offS + k;
+    offL += r->nnz_L;
+    offU += r->nnz_U;
+    offS += ns[k];
+  }
+  if (p->B == 0) delete blk;
+  return GSOFA_OK;
+}
+
+int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
+              const gsofa_options& o, cudaStream_t st, gsofa_result* outs) {
+  for (int32_t k = 0; k < count; k++) zero_result(&outs[k]);
+  // members: matrices whose every source fits the shared-memory tier together
+  const int stat = trav_smem_static_bytes();
+  const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
+  std::vector<int32_t> idx(count);
+  for (int32_t k = 0; k < count; k++) {
+    if (n[k] < 0 || !rp[k] || (n[k] > 0 && !ci[k])) return GSOFA_E_INVAL;
+    idx[k] = k;
+  }
+  std::vector<int32_t> members, singles;
+  for (int32_t k = 0; k < count; k++) {
+    const int32_t nk = n[k];
+    if (nk == 0) { singles.push_back(k); continue; }
+    const int l16 = nk <= 65533 ? 1 : 0;
+    if (o.smem_max_source == 0 && trav_smem_max_S(nk, limit, l16) >= nk) members.push_back(k);
+    else singles.push_back(k);
+  }
+  int launches = 0;
+  int rc = GSOFA_OK;
+  if (!members.empty()) rc = run_batch_members(c, members, n, rp, ci, o, st, outs, &launches);
+  for (size_t j = 0; rc == GSOFA_OK && j < singles.size(); j++) {
+    const int32_t k = singles[j];
+    rc = run_device(c, n[k], rp[k], ci[k], o, st, &outs[k]);
+    if (rc == GSOFA_OK) launches += outs[k].stats.kernel_launches;
+  }
+  if (rc != GSOFA_OK) {
+    for (int32_t k = 0; k < count; k++) gsofa_free(&outs[k]);
+    return rc;
+  }
+  if (count > 0) outs[0].stats.kernel_launches = launches;
+  return GSOFA_OK;
+}
+
 }  // namespace
 }  // namespace gsofa
 
@@ -618,7 +1155,17 @@ int gsofa_default_options(gsofa_options* opt) {
 void gsofa_free(gsofa_result* res) {
   if (!res) return;
   Priv* pv = (Priv*)res->_priv;
-  if (res->on_device) {
+  if (res->on_device && pv && pv->shared) {
+    SharedBlock* b = pv->shared;
+    if (b->refs.fetch_sub(1) == 1) {
+      int cur = -1;
+      cudaGetDevice(&cur);
+      if (cur != b->device) cudaSetDevice(b->device);
+      for (void* q : b->ptrs) cudaFreeAsync(q, b->stream);
+      if (cur != b->device && cur >= 0) cudaSetDevice(cur);
+      delete b;
+    }
+  } else if (res->on_device) {
     cudaStream_t st = pv ? pv->stream : nullptr;
     int cur = -1;
     cudaGetDevice(&cur);
@@ -740,14 +1287,13 @@ int gsofa_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colidx, cons
 int gsofa_batch(int32_t count, const int32_t* n, const int32_t* const* d_rowptr, const int32_t* const* d_colidx,
                 const gsofa_options* opt, void* stream, gsofa_result* outs) {
   if (count < 0 || (count > 0 && (!n || !d_rowptr || !d_colidx || !outs))) return GSOFA_E_INVAL;
-  for (int32_t k = 0; k < count; k++) {
-    const int rc = gsofa_symbolic_device(n[k], d_rowptr[k], d_colidx[k], opt, stream, &outs[k]);
-    if (rc != GSOFA_OK) {
-      for (int32_t j = 0; j < k; j++) gsofa_free(&outs[j]);
-      return rc;
-    }
-  }
-  return GSOFA_OK;
+  gsofa_options o;
+  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
+  if (count == 0) return GSOFA_OK;
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return err;
+  return run_batch(c, count, n, d_rowptr, d_colidx, o, (cudaStream_t)stream, outs);
 }
 
 }  // extern "C"

@@ -324,3 +324,211 @@ cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream
 }
 
 }  // namespace gsofa
+
+// ------------------------------------------------------------ batch helpers
+namespace gsofa {
+namespace {
+// matrix of a global row: the last descriptor whose row_base <= r
+__device__ __forceinline__ int mat_of_row(const MatDesc* mats, int nmats, long long r) {
+  int lo = 0, hi = nmats - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mats[mid].row_base <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int mat_of_chunk(const MatDesc* mats, int nmats, long long c) {
+  int lo = 0, hi = nmats - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (mats[mid].chunk_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+}  // namespace
+
+// validation of every matrix of a batch, one warp per (global) row
+__global__ void validate_batch_kernel(const MatDesc* __restrict__ mats, int32_t nmats, long long total_rows,
+                                      DevCounters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  if (gw < nmats && lane == 0 && mats[gw].rowptr[0] != 0) flag_row(ctr, ERR_ROWPTR, (int)mats[gw].row_base);
+  for (long long r = gw; r < total_rows; r += nw) {
+    const int m = mat_of_row(mats, nmats, r);
+    const MatDesc d = mats[m];
+    const int i = (int)(r - d.row_base);
+    const int rb = d.rowptr[i], re = d.rowptr[i + 1];
+    if (re < rb || rb < 0) {
+      if (lane == 0) flag_row(ctr, ERR_ROWPTR, (int)r);
+      continue;
+    }
+    bool bad_range = false, bad_order = false;
+    for (int e = rb + lane; e < re; e += 32) {
+      const int c = d.colidx[e];
+      if ((unsigned)c >= (unsigned)d.n) bad_range = true;
+      if (e > rb && d.colidx[e - 1] >= c) bad_order = true;
+    }
+    if (__any_sync(FULL, bad_range) && lane == 0) flag_row(ctr, ERR_COL_RANGE, (int)r);
+    if (__any_sync(FULL, bad_order) && lane == 0) flag_row(ctr, ERR_UNSORTED, (int)r);
+  }
+}
+
+cudaError_t launch_validate_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows, DevCounters* ctr,
+                                  cudaStream_t st) {
+  const int block = 256;
+  long long w = total_rows > nmats ? total_rows : nmats;
+  long long grid = (w * 32 + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  if (grid < 1) grid = 1;
+  validate_batch_kernel<<<(int)grid, block, 0, st>>>(mats, nmats, total_rows, ctr);
+  return cudaGetLastError();
+}
+
+// two-phase T3 detection (Section 5, Fig. 7) over the chunks of every matrix
+__global__ void supernode_batch_kernel(const MatDesc* __restrict__ mats, int32_t nmats, int32_t chunk,
+                                       const uint32_t* __restrict__ pool, const int64_t* __restrict__ row_off,
+                                       const int32_t* __restrict__ row_nL, const int32_t* __restrict__ row_nU,
+                                       int32_t* __restrict__ flags, int32_t* __restrict__ mat_nsuper,
+                                       DevCounters* ctr) {
+  extern __shared__ uint32_t bits[];
+  __shared__ int s_count;
+  if (input_error(ctr)) return;
+  const int m = mat_of_chunk(mats, nmats, blockIdx.x);
+  const MatDesc d = mats[m];
+  const long long rb = d.row_base;
+  const int c0 = (int)((long long)blockIdx.x - d.chunk_base) * chunk;
+  const int cend = min(d.n, c0 + chunk);
+  const int nwords = (chunk + 31) >> 5;
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0u;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; c0 + t < cend; t += blockDim.x) {
+    const long long g = rb + c0 + t;
+    if (t > 0 && row_nU[g] == row_nU[g - 1] - 1) atomicOr(&bits[t >> 5], 1u << (t & 31));
+  }
+  __syncthreads();
+  int local = 0;
+  for (int t = threadIdx.x; c0 + t < cend; t += blockDim.x) {
+    if (bits[t >> 5] & (1u << (t & 31))) continue;
+    int r = c0 + t;
+    flags[rb + r] = 1;
+    local++;
+    for (int u = t + 1; c0 + u < cend && (bits[u >> 5] & (1u << (u & 31))); u++) {
+      const long long g = rb + c0 + u;
+      const int64_t off = row_off[g];
+      bool has = false;
+      if (off >= 0) {
+        int lo = 0, hi = row_nL[g];
+        const uint32_t key = (uint32_t)r;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (pool[off + mid] < key) lo = mid + 1; else hi = mid;
+        }
+        has = lo < row_nL[g] && pool[off + lo] == key;
+      }
+      if (has) {
+        flags[g] = 0;
+      } else {
+        flags[g] = 1;
+        r = c0 + u;
+        local++;
+      }
+    }
+  }
+  if (local) atomicAdd(&s_count, local);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_count) {
+    atomicAdd(&mat_nsuper[m], s_count);
+    atomicAdd(&ctr->n_super, s_count);
+  }
+}
+
+cudaError_t launch_supernode_batch(const MatDesc* mats, int32_t nmats, int64_t total_chunks, int32_t chunk,
+                                   const uint32_t* pool, const int64_t* row_off, const int32_t* row_nL,
+                                   const int32_t* row_nU, int32_t* flags, int32_t* mat_nsuper, DevCounters* ctr,
+                                   cudaStream_t st) {
+  if (total_chunks <= 0) return cudaSuccess;
+  const int block = chunk >= 1024 ? 1024 : ((chunk + 31) / 32) * 32;
+  const size_t sm = (size_t)((chunk + 31) / 32) * 4;
+  supernode_batch_kernel<<<(unsigned)total_chunks, block, sm, st>>>(mats, nmats, chunk, pool, row_off, row_nL,
+                                                                   row_nU, flags, mat_nsuper, ctr);
+  return cudaGetLastError();
+}
+
+// per-matrix row pointers from the global exclusive scan G (length total+1):
+// matrix m's rowptr occupies out[row_base + m .. row_base + m + n] and starts at 0
+__global__ void rebase_rowptr_kernel(const MatDesc* __restrict__ mats, int32_t nmats, long long total_rows,
+                                     const int64_t* __restrict__ G, int64_t* __restrict__ out) {
+  const long long total = total_rows + nmats;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    // x = row_base[m] + m + i with 0 <= i <= n_m
+    int lo = 0, hi = nmats - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mats[mid].row_base + mid <= x) lo = mid; else hi = mid - 1;
+    }
+    const long long rb = mats[lo].row_base;
+    const long long i = x - rb - lo;
+    out[x] = G[rb + i] - G[rb];
+  }
+}
+
+cudaError_t launch_rebase_rowptr(const MatDesc* mats, int32_t nmats, int64_t total_rows, const int64_t* G,
+                                 int64_t* out, cudaStream_t st) {
+  const int block = 256;
+  long long grid = (total_rows + nmats + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  if (grid < 1) grid = 1;
+  rebase_rowptr_kernel<<<(int)grid, block, 0, st>>>(mats, nmats, total_rows, G, out);
+  return cudaGetLastError();
+}
+
+// super_start of matrix m lives at P[row_base_m] + m; its last entry is n_m
+__global__ void scatter_starts_batch_kernel(const MatDesc* __restrict__ mats, int32_t nmats, long long total_rows,
+                                            const int32_t* __restrict__ flags, const int64_t* __restrict__ P,
+                                            int32_t* __restrict__ super_start) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total_rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    if (!flags[r]) continue;
+    const int m = mat_of_row(mats, nmats, r);
+    super_start[P[r] + m] = (int32_t)(r - mats[m].row_base);
+  }
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < nmats;
+       m += (long long)gridDim.x * blockDim.x) {
+    const long long end = mats[m].row_base + mats[m].n;
+    super_start[P[end] + m] = mats[m].n;
+  }
+}
+
+cudaError_t launch_scatter_starts_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows,
+                                        const int32_t* flags, const int64_t* pos, int32_t* super_start,
+                                        cudaStream_t st) {
+  const int block = 256;
+  long long w = total_rows > nmats ? total_rows : nmats;
+  long long grid = (w + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  if (grid < 1) grid = 1;
+  scatter_starts_batch_kernel<<<(int)grid, block, 0, st>>>(mats, nmats, total_rows, flags, pos, super_start);
+  return cudaGetLastError();
+}
+
+size_t scan_tmp_bytes_long(int64_t n) {
+  const long long parts = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return (size_t)(parts > 0 ? parts : 1) * sizeof(long long);
+}
+
+cudaError_t launch_scan_i32_i64_long(const int32_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t st) {
+  if (n > INT32_MAX - SCAN_TILE) return cudaErrorInvalidValue;
+  return launch_scan_i32_i64(in, out, (int32_t)n, tmp, st);
+}
+
+cudaError_t launch_compact_long(int64_t nrows, const uint32_t* pool, const int64_t* row_off, const int32_t* row_nL,
+                                const int32_t* row_nU, const int64_t* L_off, const int64_t* U_off,
+                                int32_t* L_colidx, int32_t* U_colidx, cudaStream_t st) {
+  if (nrows > INT32_MAX) return cudaErrorInvalidValue;
+  return launch_compact((int32_t)nrows, pool, row_off, row_nL, row_nU, L_off, U_off, L_colidx, U_colidx, st);
+}
+
+}  // namespace gsofa

@@ -39,6 +39,17 @@ __device__ __forceinline__ int input_error(const DevCounters* c) {
   return *(const volatile int32_t*)&c->err & ERR_INPUT;
 }
 
+// One matrix of a batch: its CSR and where its rows sit in the concatenated
+// per-row arrays (row_base) and in the concatenated supernode chunks.
+struct MatDesc {
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  int32_t n;
+  int32_t pad;
+  int64_t row_base;
+  int64_t chunk_base;
+};
+
 // Arguments of the traversal kernels (Section 4, Fig. 5).
 struct TravArgs {
   int32_t n;
@@ -60,6 +71,15 @@ struct TravArgs {
   int32_t fill_first;                 // optional "line 9.5" of Section 4
   int32_t collect_stats;
   int32_t counts_only;                // 1: write per-row counts only (no pool, no row_off)
+  // batch mode (mats != nullptr): item k -> source s (descending) and matrix m;
+  // item_start[s] = number of items with a larger source index, mat_order lists
+  // matrices by decreasing order n; n above is the largest order in the batch
+  const MatDesc* mats;
+  const int32_t* item_start;
+  const int32_t* mat_order;
+  int32_t nmats;
+  int32_t chunk;                      // work items taken per fetch (>= 1)
+  unsigned long long* mat_tot;        // per matrix: [sum nnz(L(i,:)), sum nnz(U(i,:))]
   // global tier: per-slot working arrays (slot = CTA index)
   uint32_t* g_lab;                    // slots x n (epoch-encoded maxId)
   int32_t* g_queue;                   // slots x 2n (current / next frontier)
@@ -80,6 +100,22 @@ cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStrea
 
 cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,
                             DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_validate_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows, DevCounters* ctr,
+                                  cudaStream_t st);
+cudaError_t launch_supernode_batch(const MatDesc* mats, int32_t nmats, int64_t total_chunks, int32_t chunk,
+                                   const uint32_t* pool, const int64_t* row_off, const int32_t* row_nL,
+                                   const int32_t* row_nU, int32_t* flags, int32_t* mat_nsuper, DevCounters* ctr,
+                                   cudaStream_t st);
+cudaError_t launch_rebase_rowptr(const MatDesc* mats, int32_t nmats, int64_t total_rows, const int64_t* G,
+                                 int64_t* out, cudaStream_t st);
+cudaError_t launch_scatter_starts_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows,
+                                        const int32_t* flags, const int64_t* pos, int32_t* super_start,
+                                        cudaStream_t st);
+cudaError_t launch_scan_i32_i64_long(const int32_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t st);
+size_t scan_tmp_bytes_long(int64_t n);
+cudaError_t launch_compact_long(int64_t nrows, const uint32_t* pool, const int64_t* row_off, const int32_t* row_nL,
+                                const int32_t* row_nU, const int64_t* L_off, const int64_t* U_off,
+                                int32_t* L_colidx, int32_t* U_colidx, cudaStream_t st);
 
 // exclusive scan of int32 counts into int64 offsets (out has n+1 entries)
 size_t scan_tmp_bytes(int32_t n);

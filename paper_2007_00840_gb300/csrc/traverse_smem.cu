@@ -139,18 +139,22 @@ size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
 template <typename LabT>
 __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n = a.n, S = a.S, CAP = a.list_cap;
-  const int SW = (S + 31) >> 5, NW = (n + 31) >> 5;
+  const int n_max = a.n, S = a.S, CAP = a.list_cap;
+  const int SW = (S + 31) >> 5, NWmax = (n_max + 31) >> 5;
   LabT* lab = (LabT*)smraw;
   uint32_t* D0 = (uint32_t*)(smraw + align16(sizeof(LabT) * (size_t)S));
   uint32_t* D1 = D0 + SW;
   uint32_t* ub = D1 + SW;
-  LabT* L0 = (LabT*)(ub + NW);
+  LabT* L0 = (LabT*)(ub + NWmax);
   LabT* L1 = L0 + CAP;
   int32_t* S0 = a.spill + (size_t)blockIdx.x * 2 * (size_t)a.spill_cap;
   int32_t* S1 = S0 + a.spill_cap;
 
-  __shared__ int s_src, s_diag;
+  __shared__ int s_src, s_diag, s_n;
+  __shared__ const int32_t* s_rp;
+  __shared__ const int32_t* s_ci;
+  __shared__ long long s_rowb;
+  __shared__ int s_mat;
   __shared__ int s_q[3];
   __shared__ int s_wcL[32], s_wcU[32];
   __shared__ long long s_off;
@@ -162,24 +166,62 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
 
   for (int i = tid; i < S; i += nthr) lab[i] = (LabT)LabOps<LabT>::MAXV;
   for (int i = tid; i < SW; i += nthr) { D0[i] = 0u; D1[i] = 0u; }
-  for (int i = tid; i < NW; i += nthr) ub[i] = 0u;
+  for (int i = tid; i < NWmax; i += nthr) ub[i] = 0u;
 
   // window base of the previous source; MAXV stands for the fill value
   uint32_t base = LabOps<LabT>::MAXV;
   unsigned long long n_exp = 0, n_edge = 0;
+  int my_k = 0, my_left = 0;  // thread 0's current chunk of work items
   int bad = 0;
 
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      const int k = atomicAdd(&a.ctr->work_smem, 1);
-      s_src = (k < a.nsrc && !input_error(a.ctr)) ? (a.order ? a.order[k] : a.nsrc - 1 - k) : -1;
+      if (my_left == 0) {  // take the next chunk of work items
+        const int chunk = a.chunk > 0 ? a.chunk : 1;
+        my_k = atomicAdd(&a.ctr->work_smem, chunk);
+        my_left = chunk;
+      }
+      const int k = my_k++;
+      my_left--;
+      int src = -1;
+      if (k < a.nsrc && !input_error(a.ctr)) {
+        if (a.mats) {
+          // source index: smallest s with item_start[s] <= k (item_start decreases in s)
+          int lo = 0, hi = n_max - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.item_start[mid] <= k) hi = mid; else lo = mid + 1;
+          }
+          src = lo;
+          const int m = a.mat_order[k - a.item_start[lo]];
+          const MatDesc d = a.mats[m];
+          s_rp = d.rowptr;
+          s_ci = d.colidx;
+          s_n = d.n;
+          s_rowb = d.row_base;
+          s_mat = m;
+        } else {
+          src = a.order ? a.order[k] : a.nsrc - 1 - k;
+          s_rp = a.rowptr;
+          s_ci = a.colidx;
+          s_n = a.n;
+          s_rowb = 0;
+          s_mat = 0;
+        }
+      }
+      s_src = src;
       s_diag = 0;
       s_q[0] = s_q[1] = s_q[2] = 0;
     }
     __syncthreads();
     const int s = s_src;
     if (s < 0) break;
+    const int n = s_n;
+    const int NW = (n + 31) >> 5;
+    const int32_t* __restrict__ rowptr = s_rp;
+    const int32_t* __restrict__ colidx = s_ci;
+    const long long rowb = s_rowb;
 
     // maxId window of this source: encoded values base+1+l for l in [-1, s),
     // strictly below every value an earlier source left behind
@@ -193,9 +235,9 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     }
 
     // seed: neighbours of s; those below s form frontier 0 with maxId -1
-    const int rb = __ldg(a.rowptr + s), re = __ldg(a.rowptr + s + 1);
+    const int rb = __ldg(rowptr + s), re = __ldg(rowptr + s + 1);
     for (int e = rb + tid; e < re; e += nthr) {
-      const int w = __ldg(a.colidx + e);
+      const int w = __ldg(colidx + e);
       if ((unsigned)w >= (unsigned)n) { bad = 1; continue; }
       if (w < s) {
         lab[w] = (LabT)base;  // encoded -1
@@ -232,8 +274,8 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         if (r < qc) {
           v = r < CAP ? (int)Lc[r] : Sc[r - CAP];
           atomicAnd(&Dc[v >> 5], ~(1u << (v & 31)));  // v leaves the current list
-          eb = __ldg(a.rowptr + v);
-          ee = __ldg(a.rowptr + v + 1);
+          eb = __ldg(rowptr + v);
+          ee = __ldg(rowptr + v + 1);
           const uint32_t lv = (uint32_t)lab[v];
           const uint32_t vE = base + 1u + (uint32_t)v;
           nmE = lv > vE ? lv : vE;  // encoded max(maxId(v), v)
@@ -245,7 +287,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         for (int k0 = 0; k0 < maxdeg; k0 += BATCH) {
           int wv[BATCH];  // independent loads first, then the relaxations
 #pragma unroll
-          for (int q = 0; q < BATCH; q++) wv[q] = (k0 + q < deg) ? __ldg(a.colidx + eb + k0 + q) : 0;
+          for (int q = 0; q < BATCH; q++) wv[q] = (k0 + q < deg) ? __ldg(colidx + eb + k0 + q) : 0;
 #pragma unroll
           for (int q = 0; q < BATCH; q++) {
             const int enq = (k0 + q < deg) ? relax(c, wv[q], nmE, &bad) : 0;
@@ -260,7 +302,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           const uint32_t bnm = __shfl_sync(FULL, nmE, l);
           for (int e0 = beb; e0 < bee; e0 += 32) {
             const int e = e0 + lane;
-            const int w = e < bee ? __ldg(a.colidx + e) : 0;
+            const int w = e < bee ? __ldg(colidx + e) : 0;
             const int enq = e < bee ? relax(c, w, bnm, &bad) : 0;
             append(c, enq, w, lane);
           }
@@ -314,17 +356,21 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       if (!a.counts_only) {
         off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
         ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
-        a.row_off[s] = ok ? (int64_t)off : -1;
+        a.row_off[rowb + s] = ok ? (int64_t)off : -1;
         if (ok) a.pool[off + nL] = (uint32_t)s;
         else atomicOr(&a.ctr->err, ERR_OVERFLOW);
       }
       s_off = ok ? (long long)off : -1LL;
       s_nL = nL;
-      a.row_nL[s] = nL;
-      a.row_nU[s] = nU;
-      a.fill_count[s] = nL + nU - ((re - rb) + (s_diag ? 0 : 1));
+      a.row_nL[rowb + s] = nL;
+      a.row_nU[rowb + s] = nU;
+      a.fill_count[rowb + s] = nL + nU - ((re - rb) + (s_diag ? 0 : 1));
       atomicAdd(&a.ctr->total_L, (unsigned long long)nL);
       atomicAdd(&a.ctr->total_U, (unsigned long long)nU);
+      if (a.mat_tot) {
+        atomicAdd(&a.mat_tot[2 * s_mat], (unsigned long long)nL);
+        atomicAdd(&a.mat_tot[2 * s_mat + 1], (unsigned long long)nU);
+      }
     }
     __syncthreads();
     const long long off = s_off;
