@@ -67,7 +67,9 @@ typedef struct gsofa_options {
                                     the fastest; 0 = heuristic shape */
     int32_t work_chunk;          /* work items a CTA takes per fetch (default 1) */
     int32_t list_capacity;       /* frontier list entries kept in shared memory (default: as many as fit) */
-    int32_t reserved[4];
+    int32_t max_ctas;            /* cap on traversal CTAs per launch, so concurrent launches share the GPU
+                                    (default 0: one full wave) */
+    int32_t reserved[3];
 } gsofa_options;
 
 /* Per-call statistics (filled when options.collect_stats == 1). */
@@ -166,6 +168,57 @@ int gsofa_batch(int32_t count, const int32_t *n, const int32_t *const *d_rowptr,
 #define GSOFA_NOALLOC_SCRATCH_BYTES (16u << 20)
 int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
                              int32_t *d_nnzL, int32_t *d_nnzU, int32_t *d_fill_count, void *stream);
+
+/*
+ * Serving (spec extension of the Section 4/5 method): a request loop
+ * that factors incoming sparsity patterns with continuous batching.
+ * Requests are admitted in arrival order while their projected device memory
+ * (CSR copy, per-row workspace, row pool and outputs, label slots of large
+ * orders) fits under mem_cap_bytes; each of `streams` slots runs the admitted
+ * requests waiting at that moment (up to max_batch) as one multi-matrix batch,
+ * and the batches of different slots overlap on the GPU (each limited to
+ * opts.max_ctas traversal CTAs; 0 = 4 x SMs / streams).
+ */
+typedef struct gsofa_server gsofa_server;
+
+typedef struct gsofa_server_config {
+    int64_t mem_cap_bytes;       /* admission cap on projected device memory (default 150 GiB) */
+    int32_t max_inflight;        /* admitted, unfinished requests at most (default 8192) */
+    int32_t streams;             /* concurrent batch slots (default 3, at most 16) */
+    int32_t max_batch;           /* requests per batch launch (default 512) */
+    int32_t queue_capacity;      /* pending requests before submit returns GSOFA_E_BUSY (default 2^20) */
+    gsofa_options opts;          /* options of every batch */
+} gsofa_server_config;
+
+typedef struct gsofa_server_stats {
+    int64_t completed, failed, batches, pending;
+    int32_t inflight, pad;
+    int64_t total_nnz;           /* nnz(L+U) of completed requests */
+    int64_t total_rows;          /* rows of completed requests */
+    int64_t mem_in_use, peak_mem_in_use;   /* projected bytes of admitted requests */
+    float p50_ms, p99_ms, max_ms;          /* latency, submission to completed result */
+    float pad2;
+    double span_s;               /* first submission to last completion */
+} gsofa_server_stats;
+
+int gsofa_server_default_config(gsofa_server_config *cfg);
+/* Start the dispatcher threads on the current device. */
+int gsofa_server_create(const gsofa_server_config *cfg, gsofa_server **server);
+/* Queue one pattern.  on_device = 1: rowptr/colidx are device pointers; 0: host
+ * pointers (copied at dispatch).  Either way the buffers must stay valid and
+ * unchanged until the request completes.  GSOFA_E_BUSY when the queue is full,
+ * GSOFA_E_NOMEM when the request alone exceeds the cap. */
+int gsofa_server_submit(gsofa_server *server, int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                        int32_t on_device, uint64_t *ticket);
+/* Non-blocking: GSOFA_OK moves the device result to *out (release with gsofa_free;
+ * out may be NULL to discard it), GSOFA_E_PENDING if not finished, GSOFA_E_NOTFOUND. */
+int gsofa_server_poll(gsofa_server *server, uint64_t ticket, gsofa_result *out, double *latency_ms);
+/* Blocking variant of poll with a timeout in seconds (GSOFA_E_TIMEOUT). */
+int gsofa_server_wait(gsofa_server *server, uint64_t ticket, double timeout_s, gsofa_result *out,
+                      double *latency_ms);
+int gsofa_server_get_stats(gsofa_server *server, gsofa_server_stats *stats);
+/* Finish admitted requests, drop pending ones, free unclaimed results. */
+void gsofa_server_destroy(gsofa_server *server);
 
 /* Release every array of *res (device or host) and zero it.  NULL-safe.
  * Device arrays are freed stream-ordered on the stream of the call that made

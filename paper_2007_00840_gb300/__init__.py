@@ -18,8 +18,8 @@ import numpy as np
 from . import _lib
 from ._lib import GsofaError, gsofa_options, gsofa_result
 
-__all__ = ["options", "symbolic_device", "symbolic_host", "batch_device", "DeviceResult", "HostResult",
-           "GsofaError", "load", "version"]
+__all__ = ["options", "symbolic_device", "symbolic_host", "batch_device", "row_counts_noalloc", "Server",
+           "DeviceResult", "HostResult", "GsofaError", "load", "version"]
 
 load = _lib.load
 
@@ -216,3 +216,104 @@ def batch_device(mats, opts: gsofa_options | None = None, stream=None) -> list:
         ctypes.pointer(r)[0] = outs[i]
         res.append(DeviceResult(r, sh))
     return res
+
+
+def row_counts_noalloc(rowptr, colidx, nnzL, nnzU, fill_count, stream=None) -> None:
+    """gsofa_row_counts_noalloc into caller-provided int32 CUDA tensors (no device allocation)."""
+    lib = load()
+    n = int(rowptr.numel() - 1)
+    rc = lib.gsofa_row_counts_noalloc(n, ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(colidx.data_ptr()),
+                                      ctypes.c_void_p(nnzL.data_ptr()), ctypes.c_void_p(nnzU.data_ptr()),
+                                      ctypes.c_void_p(fill_count.data_ptr()), ctypes.c_void_p(_stream_handle(stream)))
+    if rc != 0:
+        raise GsofaError(rc, -1, "gsofa_row_counts_noalloc")
+
+
+class Server:
+    """Continuous-batching server (gsofa_server_*).  Inputs must stay alive until collected."""
+
+    def __init__(self, mem_cap_bytes: int = 0, streams: int = 0, max_batch: int = 0, max_inflight: int = 0,
+                 queue_capacity: int = 0, opts: gsofa_options | None = None):
+        lib = load()
+        cfg = _lib.gsofa_server_config()
+        lib.gsofa_server_default_config(ctypes.byref(cfg))
+        if mem_cap_bytes:
+            cfg.mem_cap_bytes = mem_cap_bytes
+        if streams:
+            cfg.streams = streams
+        if max_batch:
+            cfg.max_batch = max_batch
+        if max_inflight:
+            cfg.max_inflight = max_inflight
+        if queue_capacity:
+            cfg.queue_capacity = queue_capacity
+        if opts is not None:
+            cfg.opts = opts
+        h = ctypes.c_void_p()
+        rc = lib.gsofa_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != 0:
+            raise GsofaError(rc, -1, "gsofa_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, rowptr, colidx) -> int:
+        """Queue a pattern: int32 CUDA tensors (device-resident) or numpy arrays (host)."""
+        lib = load()
+        t = ctypes.c_uint64()
+        if hasattr(rowptr, "is_cuda") and rowptr.is_cuda:
+            n = int(rowptr.numel() - 1)
+            rc = lib.gsofa_server_submit(self._h, n, ctypes.c_void_p(rowptr.data_ptr()),
+                                         ctypes.c_void_p(colidx.data_ptr() if colidx.numel() else rowptr.data_ptr()),
+                                         1, ctypes.byref(t))
+        else:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+            if colidx.size == 0:
+                colidx = np.zeros(1, np.int32)
+            rc = lib.gsofa_server_submit(self._h, int(rowptr.size - 1), rowptr.ctypes.data_as(ctypes.c_void_p),
+                                         colidx.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(t))
+        if rc != 0:
+            raise GsofaError(rc, -1, "gsofa_server_submit")
+        self._keep[t.value] = (rowptr, colidx)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(DeviceResult, latency_ms) if finished, else None."""
+        lib = load()
+        r = gsofa_result()
+        lat = ctypes.c_double()
+        rc = lib.gsofa_server_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(lat))
+        if rc == _lib.GSOFA_E_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        if rc != 0:
+            raise GsofaError(rc, -1, "gsofa_server_poll")
+        return DeviceResult(r, 0), lat.value
+
+    def wait(self, ticket: int, timeout: float = 600.0, keep_result: bool = True):
+        lib = load()
+        r = gsofa_result()
+        lat = ctypes.c_double()
+        rc = lib.gsofa_server_wait(self._h, ctypes.c_uint64(ticket), timeout,
+                                   ctypes.byref(r) if keep_result else None, ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        if rc != 0:
+            raise GsofaError(rc, -1, "gsofa_server_wait")
+        return (DeviceResult(r, 0) if keep_result else None), lat.value
+
+    def stats(self) -> dict:
+        st = _lib.gsofa_server_stats()
+        load().gsofa_server_get_stats(self._h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in st._fields_ if not f.startswith("pad")}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gsofa_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

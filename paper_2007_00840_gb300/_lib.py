@@ -33,7 +33,8 @@ class gsofa_options(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("work_chunk", ctypes.c_int32),
         ("list_capacity", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("max_ctas", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -73,6 +74,37 @@ class gsofa_result(ctypes.Structure):
     ]
 
 
+class gsofa_server_config(ctypes.Structure):
+    _fields_ = [
+        ("mem_cap_bytes", ctypes.c_int64),
+        ("max_inflight", ctypes.c_int32),
+        ("streams", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("queue_capacity", ctypes.c_int32),
+        ("opts", gsofa_options),
+    ]
+
+
+class gsofa_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("pending", ctypes.c_int64),
+        ("inflight", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("total_nnz", ctypes.c_int64),
+        ("total_rows", ctypes.c_int64),
+        ("mem_in_use", ctypes.c_int64),
+        ("peak_mem_in_use", ctypes.c_int64),
+        ("p50_ms", ctypes.c_float),
+        ("p99_ms", ctypes.c_float),
+        ("max_ms", ctypes.c_float),
+        ("pad2", ctypes.c_float),
+        ("span_s", ctypes.c_double),
+    ]
+
+
 # every symbol include/gsofa.h declares, with its ctypes signature
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -83,6 +115,15 @@ SIGNATURES = {
                                              ctypes.POINTER(gsofa_result)]),
     "gsofa_batch": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(gsofa_options), _P, _P]),
     "gsofa_row_counts_noalloc": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P]),
+    "gsofa_server_default_config": (ctypes.c_int, [ctypes.POINTER(gsofa_server_config)]),
+    "gsofa_server_create": (ctypes.c_int, [ctypes.POINTER(gsofa_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "gsofa_server_submit": (ctypes.c_int, [_P, _I32, _P, _P, _I32, ctypes.POINTER(ctypes.c_uint64)]),
+    "gsofa_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(gsofa_result),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "gsofa_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(gsofa_result),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "gsofa_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gsofa_server_stats)]),
+    "gsofa_server_destroy": (None, [_P]),
     "gsofa_free": (None, [ctypes.POINTER(gsofa_result)]),
     "gsofa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gsofa_version": (ctypes.c_int, []),

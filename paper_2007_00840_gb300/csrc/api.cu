@@ -324,11 +324,13 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     p->list_cap = cap;
     p->smem_block = block;
     p->smem_grid = c->sms * occ;
+    if (o.max_ctas > 0 && o.max_ctas < p->smem_grid) p->smem_grid = o.max_ctas;
   }
   if (S < n) {
     int block = o.threads_per_source > 0 ? o.threads_per_source : 512;
     p->glob_block = block;
     int slots = o.max_concurrent > 0 ? o.max_concurrent : c->sms;
+    if (o.max_ctas > 0 && o.max_ctas < slots) slots = o.max_ctas;
     p->glob_grid = slots;
   }
   return GSOFA_OK;
@@ -350,6 +352,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->max_concurrent = in->max_concurrent;
   o->mem_budget_bytes = in->mem_budget_bytes;
   if (in->work_chunk < 0 || in->list_capacity < 0) return GSOFA_E_INVAL;
+  if (in->max_ctas < 0) return GSOFA_E_INVAL;
+  o->max_ctas = in->max_ctas;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -614,6 +618,10 @@ struct LaunchShape {
 
 // Workspace and captured graph of one batch signature.
 struct BatchPlan {
+  bool transient = false;           // workspace from the stream-ordered pool, freed after one call
+  cudaStream_t stream = nullptr;
+  Ctx* ctx = nullptr;
+  int max_ctas = 0;
   uint64_t sig = 0;
   uint64_t last_use = 0;
   int32_t B = 0;                    // matrices in the batched launch
@@ -639,6 +647,7 @@ struct BatchPlan {
   int grid = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the traversal launch (collect_stats)
 
   DevCounters* ctr() const { return (DevCounters*)d_ctr; }
   unsigned long long* mat_tot() const { return (unsigned long long*)(d_ctr + 256); }
@@ -649,7 +658,19 @@ struct BatchPlan {
 };
 
 void free_plan(BatchPlan* p) {
+  if (p->transient) {
+    for (void* q : {(void*)p->d_mats, (void*)p->d_item_start, (void*)p->d_mat_order, (void*)p->d_ctr,
+                    (void*)p->row_off, (void*)p->row_nL, (void*)p->row_nU, (void*)p->flags, (void*)p->fill,
+                    (void*)p->pool, (void*)p->spill})
+      if (q) cudaFreeAsync(q, p->stream);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    delete p;
+    return;
+  }
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
   cudaFree(p->d_mats);
   cudaFree(p->d_item_start);
   cudaFree(p->d_mat_order);
@@ -765,9 +786,10 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.nmats = p.B;
   a.chunk = p.shape.work_chunk;
   a.mat_tot = p.mat_tot();
-  if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
+  // external records become event nodes when this sequence is captured into a graph
+  if (t0 && (e = cudaEventRecordWithFlags(t0, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) return e;
-  if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
+  if (t1 && (e = cudaEventRecordWithFlags(t1, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   if ((e = launch_supernode_batch(p.d_mats, p.B, p.chunks, o.chunk_size, p.pool, p.row_off, p.row_nL, p.row_nU,
                                   p.flags, p.mat_nsuper(), p.ctr(), st)) != cudaSuccess)
     return e;
@@ -777,14 +799,18 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
 int set_shape(Ctx* c, BatchPlan* p, const LaunchShape& sh) {
   p->shape = sh;
   p->grid = c->sms * sh.occ;
+  if (p->max_ctas > 0 && p->max_ctas < p->grid) p->grid = p->max_ctas;
   // per CTA two overflow lists of (n_max - list capacity) entries
   p->spill_cap = p->n_max > sh.list_cap ? (int64_t)p->n_max - sh.list_cap : 1;
   const int64_t need = (int64_t)p->grid * 2 * p->spill_cap;
   if (!p->spill || need > p->spill_alloc) {
-    cudaFree(p->spill);
+    if (p->transient) cudaFreeAsync(p->spill, p->stream); else cudaFree(p->spill);
     p->spill = nullptr;
     p->spill_alloc = 0;
-    if (cudaMalloc(&p->spill, sizeof(int32_t) * (size_t)need) != cudaSuccess) {
+    const cudaError_t ea = p->transient
+        ? cudaMallocFromPoolAsync((void**)&p->spill, sizeof(int32_t) * (size_t)need, c->mpool, p->stream)
+        : cudaMalloc(&p->spill, sizeof(int32_t) * (size_t)need);
+    if (ea != cudaSuccess) {
       cudaGetLastError();
       p->spill = nullptr;
       return GSOFA_E_NOMEM;
@@ -798,10 +824,38 @@ int set_shape(Ctx* c, BatchPlan* p, const LaunchShape& sh) {
   return GSOFA_OK;
 }
 
+// Pinned host scratch of the calling thread (descriptor uploads, size read-backs
+// of transient batches); reused once the previous call on this thread waited.
+void* thread_pinned(size_t bytes, int slot) {
+  thread_local void* buf[2] = {nullptr, nullptr};
+  thread_local size_t cap[2] = {0, 0};
+  if (cap[slot] < bytes) {
+    if (buf[slot]) cudaFreeHost(buf[slot]);
+    buf[slot] = nullptr;
+    cap[slot] = 0;
+    const size_t want = bytes + (bytes >> 1) + 4096;
+    if (cudaMallocHost(&buf[slot], want) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cap[slot] = want;
+  }
+  return buf[slot];
+}
+
 int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
-               const int32_t* const* ci, const gsofa_options& o, uint64_t sig, BatchPlan** out) {
+               const int32_t* const* ci, const gsofa_options& o, uint64_t sig, BatchPlan** out,
+               bool transient, cudaStream_t st) {
   BatchPlan* p = new BatchPlan();
+  p->transient = transient;
+  p->stream = st;
+  p->ctx = c;
+  p->max_ctas = o.max_ctas;
   p->sig = sig;
+  if (o.collect_stats) {
+    cudaEventCreate(&p->ev0);
+    cudaEventCreate(&p->ev1);
+  }
   p->members = members;
   p->B = (int32_t)members.size();
   std::vector<MatDesc> mats(p->B);
@@ -847,6 +901,42 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
     std::lock_guard<std::mutex> lk(c->hmu);
     auto it = c->pool_hint.find(-(int32_t)(sig & 0x7FFFFFFF) - 1);
     p->pool_cap = it != c->pool_hint.end() ? it->second : 64 * p->N + (1 << 20);
+  }
+  if (transient) {
+    const size_t b_mats = sizeof(MatDesc) * (size_t)(p->B > 0 ? p->B : 1);
+    const size_t b_is = sizeof(int32_t) * item_start.size();
+    const size_t b_ord = sizeof(int32_t) * (size_t)(p->B > 0 ? p->B : 1);
+    unsigned char* stage = (unsigned char*)thread_pinned(b_mats + b_is + b_ord, 0);
+    p->h_ctr = (unsigned char*)thread_pinned(p->ctr_bytes, 1);
+    bool ok = stage && p->h_ctr &&
+              palloc(c, &p->d_mats, (size_t)(p->B > 0 ? p->B : 1), st) == cudaSuccess &&
+              palloc(c, &p->d_item_start, item_start.size(), st) == cudaSuccess &&
+              palloc(c, &p->d_mat_order, (size_t)(p->B > 0 ? p->B : 1), st) == cudaSuccess &&
+              palloc(c, &p->d_ctr, p->ctr_bytes, st) == cudaSuccess &&
+              palloc(c, &p->row_off, (size_t)p->N, st) == cudaSuccess &&
+              palloc(c, &p->row_nL, (size_t)p->N, st) == cudaSuccess &&
+              palloc(c, &p->row_nU, (size_t)p->N, st) == cudaSuccess &&
+              palloc(c, &p->flags, (size_t)p->N, st) == cudaSuccess &&
+              palloc(c, &p->fill, (size_t)p->N, st) == cudaSuccess &&
+              palloc(c, &p->pool, (size_t)p->pool_cap, st) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      p->h_ctr = nullptr;
+      free_plan(p);
+      return GSOFA_E_NOMEM;
+    }
+    std::memcpy(stage, mats.data(), sizeof(MatDesc) * (size_t)p->B);
+    std::memcpy(stage + b_mats, item_start.data(), b_is);
+    std::memcpy(stage + b_mats + b_is, order.data(), sizeof(int32_t) * (size_t)p->B);
+    if (cudaMemcpyAsync(p->d_mats, stage, b_mats, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->d_item_start, stage + b_mats, b_is, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->d_mat_order, stage + b_mats + b_is, b_ord, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      p->h_ctr = nullptr;
+      free_plan(p);
+      return GSOFA_E_CUDA;
+    }
+    *out = p;
+    return GSOFA_OK;
   }
   bool ok = cudaMalloc(&p->d_mats, sizeof(MatDesc) * (size_t)(p->B > 0 ? p->B : 1)) == cudaSuccess &&
             cudaMalloc(&p->d_item_start, sizeof(int32_t) * item_start.size()) == cudaSuccess &&
@@ -905,7 +995,7 @@ int autotune_plan(Ctx* c, BatchPlan* p, const gsofa_options& o, cudaStream_t st,
 int capture_plan(BatchPlan* p, const gsofa_options& o) {
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return GSOFA_E_CUDA;
-  const cudaError_t e1 = enqueue_phase1(*p, o, p->cap_stream, nullptr, nullptr);
+  const cudaError_t e1 = enqueue_phase1(*p, o, p->cap_stream, p->ev0, p->ev1);
   const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || !g) {
     cudaGetLastError();
@@ -922,72 +1012,14 @@ int capture_plan(BatchPlan* p, const gsofa_options& o) {
   return GSOFA_OK;
 }
 
-// Batched path for the members that fit the shared-memory tier.
-int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
-                      const int32_t* const* ci, const gsofa_options& o, cudaStream_t st, gsofa_result* outs,
-                      int* launches) {
-  BatchCache& bc = g_batch[c->device];
-  uint64_t sig = 0x5EED;
-  for (int32_t k : members) {
-    sig = mix64(sig, (uint64_t)k);  // position in the caller's arrays
-    sig = mix64(sig, (uint64_t)n[k]);
-    sig = mix64(sig, (uint64_t)(uintptr_t)rp[k]);
-    sig = mix64(sig, (uint64_t)(uintptr_t)ci[k]);
-  }
-  sig = mix64(sig, ((uint64_t)o.chunk_size << 32) ^ ((uint64_t)o.fill_first << 8) ^ (uint64_t)o.validate);
-  sig = mix64(sig, ((uint64_t)o.work_chunk << 32) ^ ((uint64_t)o.list_capacity << 4) ^ (uint64_t)o.threads_per_source);
-  sig = mix64(sig, (uint64_t)o.collect_stats);
-  std::unique_lock<std::mutex> lk(bc.mu);  // one batch at a time per device uses a plan
-  load_tune_file(bc);
-  BatchPlan* p = nullptr;
-  auto it = bc.plans.find(sig);
-  if (it != bc.plans.end()) {
-    p = it->second;
-  } else {
-    int rc = build_plan(c, members, n, rp, ci, o, sig, &p);
-    if (rc) return rc;
-    const int stat = trav_smem_static_bytes();
-    const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
-    const uint64_t key = bucket_key(p->n_max, p->N, p->label16) ^ ((uint64_t)o.threads_per_source << 48);
-    auto tt = bc.tuned.find(key);
-    if (o.autotune && o.threads_per_source == 0 && o.list_capacity == 0 && o.work_chunk == 0 && tt == bc.tuned.end()) {
-      rc = autotune_plan(c, p, o, st, limit);
-      if (rc) { free_plan(p); return rc; }
-      bc.tuned[key] = p->shape;
-      save_tune_entry(key, p->shape);
-    } else {
-      LaunchShape sh;
-      if (tt != bc.tuned.end() && o.list_capacity == 0 && o.work_chunk == 0) {
-        sh = tt->second;
-      } else {
-        int32_t cap = 0;
-        rc = choose_smem_config(c->sms, limit, p->n_max, p->n_max, p->label16, o.threads_per_source, &sh.block,
-                                &sh.occ, &cap);
-        if (rc) { free_plan(p); return rc; }
-        if (o.list_capacity > 0 && o.list_capacity < cap) cap = o.list_capacity < 32 ? 32 : o.list_capacity;
-        sh.list_cap = cap;
-        sh.work_chunk = o.work_chunk > 0 ? o.work_chunk : 1;
-      }
-      rc = set_shape(c, p, sh);
-      if (rc) { free_plan(p); return rc; }
-    }
-    if (bc.plans.size() >= 8) {  // keep at most 8 plans: drop the least recently used
-      auto victim = bc.plans.begin();
-      for (auto jt = bc.plans.begin(); jt != bc.plans.end(); ++jt)
-        if (jt->second->last_use < victim->second->last_use) victim = jt;
-      cudaDeviceSynchronize();
-      free_plan(victim->second);
-      bc.plans.erase(victim);
-    }
-    bc.plans[sig] = p;
-  }
-  p->last_use = ++bc.clock;
-
+// Phase 1 (counters, validation, traversal, supernodes, size read-back),
+// rerun with an exact pool when the row pool overflowed.
+int batch_phase1(Ctx* c, BatchPlan* p, const gsofa_options& o, cudaStream_t st, bool use_graph, int* launches) {
   for (int attempt = 0; attempt < 3; attempt++) {
-    if (!p->gexec && capture_plan(p, o) != GSOFA_OK) {
-      // graph capture unavailable: launch directly
-      if (enqueue_phase1(*p, o, st, nullptr, nullptr) != cudaSuccess) return GSOFA_E_CUDA;
-    } else if (cudaGraphLaunch(p->gexec, st) != cudaSuccess) {
+    if (use_graph && !p->gexec && capture_plan(p, o) != GSOFA_OK) use_graph = false;
+    if (use_graph) {
+      if (cudaGraphLaunch(p->gexec, st) != cudaSuccess) return GSOFA_E_CUDA;
+    } else if (enqueue_phase1(*p, o, st, p->ev0, p->ev1) != cudaSuccess) {
       return GSOFA_E_CUDA;
     }
     *launches += 4 + (o.validate != 2 ? 1 : 0);
@@ -996,24 +1028,32 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
     const DevCounters* h = p->hctr();
     if (h->err & ERR_INPUT) return GSOFA_E_INVAL;
     if (h->err & ERR_NOCONV) return GSOFA_E_NOCONVERGE;
-    if (!(h->err & ERR_OVERFLOW)) break;
+    if (!(h->err & ERR_OVERFLOW)) return GSOFA_OK;
     // the row pool was too small; the totals are exact now
     const long long need = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
-    cudaFree(p->pool);
-    p->pool = nullptr;
-    if (cudaMalloc(&p->pool, sizeof(uint32_t) * (size_t)need) != cudaSuccess) {
+    cudaError_t ea;
+    if (p->transient) {
+      cudaFreeAsync(p->pool, st);
+      p->pool = nullptr;
+      ea = palloc(c, &p->pool, (size_t)need, st);
+    } else {
+      cudaFree(p->pool);
+      p->pool = nullptr;
+      ea = cudaMalloc(&p->pool, sizeof(uint32_t) * (size_t)need);
+    }
+    if (ea != cudaSuccess) {
       cudaGetLastError();
       p->pool_cap = 0;
-      bc.plans.erase(p->sig);
-      free_plan(p);
       return GSOFA_E_NOMEM;
     }
     p->pool_cap = need;
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-    if (attempt == 2) return GSOFA_E_NOMEM;
   }
+  return GSOFA_E_NOMEM;
+}
 
-  // phase 2: exact outputs for every member in one shared allocation
+// Phase 2: exact outputs for every member in one shared allocation.
+int batch_phase2(Ctx* c, BatchPlan* p, const int32_t* n, cudaStream_t st, gsofa_result* outs, int* launches) {
   const DevCounters* h = p->hctr();
   const int64_t total_L = (int64_t)h->total_L, total_U = (int64_t)h->total_U;
   const int64_t total_super = h->n_super;
@@ -1052,7 +1092,7 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
     delete blk;
     return ok ? GSOFA_E_CUDA : GSOFA_E_NOMEM;
   }
-  // hand out views into the block (host-side prefix sums of the per-matrix totals)
+  // views into the block (host-side prefix sums of the per-matrix totals)
   const unsigned long long* tot = p->h_tot();
   const int32_t* ns = p->h_nsuper();
   int64_t offL = 0, offU = 0, offS = 0;
@@ -1082,11 +1122,108 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
     offS += ns[k];
   }
   if (p->B == 0) delete blk;
+  if (p->ev0 && p->B > 0) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) {
+      outs[p->members[0]].stats.ms_traverse = ms;
+      outs[p->members[0]].stats.ms_traverse_smem = ms;
+    }
+    cudaGetLastError();
+  }
   return GSOFA_OK;
 }
 
+LaunchShape default_shape(Ctx* c, BatchCache& bc, const BatchPlan* p, const gsofa_options& o, size_t limit, int* rc) {
+  LaunchShape sh;
+  const uint64_t key = bucket_key(p->n_max, p->N, p->label16) ^ ((uint64_t)o.threads_per_source << 48);
+  auto tt = bc.tuned.find(key);
+  if (tt != bc.tuned.end() && o.list_capacity == 0 && o.work_chunk == 0) return tt->second;
+  int32_t cap = 0;
+  *rc = choose_smem_config(c->sms, limit, p->n_max, p->n_max, p->label16, o.threads_per_source, &sh.block, &sh.occ,
+                           &cap);
+  if (o.list_capacity > 0 && o.list_capacity < cap) cap = o.list_capacity < 32 ? 32 : o.list_capacity;
+  sh.list_cap = cap;
+  sh.work_chunk = o.work_chunk > 0 ? o.work_chunk : 1;
+  return sh;
+}
+
+// Batched path for the members that fit the shared-memory tier.  transient:
+// one-off composition (served batches): pooled workspace, no graph, no cache.
+int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
+                      const int32_t* const* ci, const gsofa_options& o, cudaStream_t st, gsofa_result* outs,
+                      int* launches, bool transient) {
+  BatchCache& bc = g_batch[c->device];
+  const int stat = trav_smem_static_bytes();
+  const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
+  if (transient) {
+    BatchPlan* p = nullptr;
+    int rc = build_plan(c, members, n, rp, ci, o, 0, &p, true, st);
+    if (rc) return rc;
+    {
+      std::lock_guard<std::mutex> lk(bc.mu);
+      load_tune_file(bc);
+      const LaunchShape sh = default_shape(c, bc, p, o, limit, &rc);
+      if (rc == GSOFA_OK) rc = set_shape(c, p, sh);
+    }
+    if (rc == GSOFA_OK) rc = batch_phase1(c, p, o, st, false, launches);
+    if (rc == GSOFA_OK) rc = batch_phase2(c, p, n, st, outs, launches);
+    free_plan(p);
+    return rc;
+  }
+  uint64_t sig = 0x5EED;
+  for (int32_t k : members) {
+    sig = mix64(sig, (uint64_t)k);  // position in the caller's arrays
+    sig = mix64(sig, (uint64_t)n[k]);
+    sig = mix64(sig, (uint64_t)(uintptr_t)rp[k]);
+    sig = mix64(sig, (uint64_t)(uintptr_t)ci[k]);
+  }
+  sig = mix64(sig, ((uint64_t)o.chunk_size << 32) ^ ((uint64_t)o.fill_first << 8) ^ (uint64_t)o.validate);
+  sig = mix64(sig, ((uint64_t)o.work_chunk << 32) ^ ((uint64_t)o.list_capacity << 4) ^ (uint64_t)o.threads_per_source);
+  sig = mix64(sig, ((uint64_t)o.collect_stats << 32) ^ (uint64_t)o.max_ctas);
+  std::unique_lock<std::mutex> lk(bc.mu);  // cached plans are used by one call at a time
+  load_tune_file(bc);
+  BatchPlan* p = nullptr;
+  auto it = bc.plans.find(sig);
+  if (it != bc.plans.end()) {
+    p = it->second;
+  } else {
+    int rc = build_plan(c, members, n, rp, ci, o, sig, &p, false, st);
+    if (rc) return rc;
+    const uint64_t key = bucket_key(p->n_max, p->N, p->label16) ^ ((uint64_t)o.threads_per_source << 48);
+    if (o.autotune && o.threads_per_source == 0 && o.list_capacity == 0 && o.work_chunk == 0 &&
+        bc.tuned.find(key) == bc.tuned.end()) {
+      rc = autotune_plan(c, p, o, st, limit);
+      if (rc) { free_plan(p); return rc; }
+      bc.tuned[key] = p->shape;
+      save_tune_entry(key, p->shape);
+    } else {
+      const LaunchShape sh = default_shape(c, bc, p, o, limit, &rc);
+      if (rc == GSOFA_OK) rc = set_shape(c, p, sh);
+      if (rc) { free_plan(p); return rc; }
+    }
+    if (bc.plans.size() >= 8) {  // keep at most 8 plans: drop the least recently used
+      auto victim = bc.plans.begin();
+      for (auto jt = bc.plans.begin(); jt != bc.plans.end(); ++jt)
+        if (jt->second->last_use < victim->second->last_use) victim = jt;
+      cudaDeviceSynchronize();
+      free_plan(victim->second);
+      bc.plans.erase(victim);
+    }
+    bc.plans[sig] = p;
+  }
+  p->last_use = ++bc.clock;
+  int rc = batch_phase1(c, p, o, st, true, launches);
+  if (rc == GSOFA_E_NOMEM) {
+    bc.plans.erase(p->sig);
+    free_plan(p);
+    return rc;
+  }
+  if (rc) return rc;
+  return batch_phase2(c, p, n, st, outs, launches);
+}
+
 int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
-              const gsofa_options& o, cudaStream_t st, gsofa_result* outs) {
+              const gsofa_options& o, cudaStream_t st, gsofa_result* outs, bool transient) {
   for (int32_t k = 0; k < count; k++) zero_result(&outs[k]);
   // members: matrices whose every source fits the shared-memory tier together
   const int stat = trav_smem_static_bytes();
@@ -1106,7 +1243,7 @@ int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp,
   }
   int launches = 0;
   int rc = GSOFA_OK;
-  if (!members.empty()) rc = run_batch_members(c, members, n, rp, ci, o, st, outs, &launches);
+  if (!members.empty()) rc = run_batch_members(c, members, n, rp, ci, o, st, outs, &launches, transient);
   for (size_t j = 0; rc == GSOFA_OK && j < singles.size(); j++) {
     const int32_t k = singles[j];
     rc = run_device(c, n[k], rp[k], ci[k], o, st, &outs[k]);
@@ -1120,6 +1257,52 @@ int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp,
   return GSOFA_OK;
 }
 
+}  // namespace
+
+// Served batches: one-off composition, pooled workspace, no graph (serve.cu).
+int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
+                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs) {
+  gsofa_options o;
+  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
+  if (count <= 0) return count == 0 ? GSOFA_OK : GSOFA_E_INVAL;
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return err;
+  return run_batch(c, count, n, rp, ci, o, st, outs, true);
+}
+
+int device_sms() {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  return c ? c->sms : 0;
+}
+
+int32_t smem_tier_max_order() {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return 0;
+  const size_t limit = (size_t)c->smem_optin - (size_t)trav_smem_static_bytes() - 64;
+  // largest n whose every source fits the shared-memory tier (16-bit labels)
+  int32_t lo = 0, hi = 65533;
+  while (lo < hi) {
+    const int32_t mid = (int32_t)(((int64_t)lo + hi + 1) / 2);
+    if (trav_smem_max_S(mid, limit, 1) >= mid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+namespace {
+}  // namespace
+
+// A completed result whose producing stream may go away: free it unordered.
+void detach_result_stream(gsofa_result* r) {
+  Priv* pv = (Priv*)r->_priv;
+  if (!pv) return;
+  pv->stream = nullptr;
+  if (pv->shared) pv->shared->stream = nullptr;
+}
+
+namespace {
 }  // namespace
 }  // namespace gsofa
 
@@ -1293,7 +1476,7 @@ int gsofa_batch(int32_t count, const int32_t* n, const int32_t* const* d_rowptr,
   int err = GSOFA_OK;
   Ctx* c = get_ctx(&err);
   if (!c) return err;
-  return run_batch(c, count, n, d_rowptr, d_colidx, o, (cudaStream_t)stream, outs);
+  return run_batch(c, count, n, d_rowptr, d_colidx, o, (cudaStream_t)stream, outs, false);
 }
 
 }  // extern "C"

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gsofa.h"
+
 namespace gsofa {
 
 // ---- device error word bits (err[0]); err[1] keeps the first offending row
@@ -136,6 +138,11 @@ cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
 cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
 
 // host helpers (api.cu)
+int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
+                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs);
+int device_sms();
+void detach_result_stream(gsofa_result* r);
+int32_t smem_tier_max_order();
 int wait_stream(cudaStream_t st);  // bounded wait; GSOFA_OK / GSOFA_E_TIMEOUT / GSOFA_E_CUDA
 int choose_smem_config(int sms, size_t limit, int32_t n, int32_t S, int label16, int threads_req, int* block,
                        int* occ, int32_t* cap);

@@ -55,6 +55,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(gsofa_options, mem_budget_bytes), offsetof(gsofa_result, L_rowptr),
          offsetof(gsofa_result, stats), offsetof(gsofa_result, _priv));
   printf("%zu %zu\n", offsetof(gsofa_stats, vertices_expanded), offsetof(gsofa_result, on_device));
+  printf("%zu %zu %zu %zu\n", sizeof(gsofa_server_config), sizeof(gsofa_server_stats),
+         offsetof(gsofa_server_config, opts), offsetof(gsofa_server_stats, span_s));
+  printf("%zu %zu\n", offsetof(gsofa_options, max_ctas), offsetof(gsofa_options, reserved));
   return 0;
 }
 """
@@ -68,6 +71,9 @@ int main(void) {
     assert vals[:3] == [ctypes.sizeof(O), ctypes.sizeof(S), ctypes.sizeof(R)]
     assert vals[3:7] == [O.mem_budget_bytes.offset, R.L_rowptr.offset, R.stats.offset, R._priv.offset]
     assert vals[7:9] == [S.vertices_expanded.offset, R.on_device.offset]
+    C, T = _lib.gsofa_server_config, _lib.gsofa_server_stats
+    assert vals[9:13] == [ctypes.sizeof(C), ctypes.sizeof(T), C.opts.offset, T.span_s.offset]
+    assert vals[13:15] == [O.max_ctas.offset, O.reserved.offset]
 
 
 def test_defaults_and_errors_without_gpu():
