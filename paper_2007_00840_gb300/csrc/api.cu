@@ -36,8 +36,8 @@ struct Ctx {
   std::mutex gmu;
   uint32_t* g_lab = nullptr;
   int32_t* g_queue = nullptr;
-  uint32_t* g_inq = nullptr;
-  uint32_t* g_rowbits = nullptr;
+  int32_t* g_list = nullptr;
+  uint32_t* g_bits = nullptr;    // P | U bitmaps and their summaries, per slot
   uint32_t* g_base = nullptr;
   int64_t g_cap = 0;
   int g_slots = 0;
@@ -185,32 +185,36 @@ void pfree(T*& p, cudaStream_t st) {
   p = nullptr;
 }
 
+// Bytes of one global-tier slot of capacity cap (a multiple of 1024 vertices).
+int64_t slot_bytes(int64_t cap) { return cap * 16 + 2 * (cap / 8 + cap / 256); }
+
 // Make sure the global-tier slots hold `slots` x `cap` vertices.  Caller holds gmu.
 int ensure_slots(Ctx* c, int64_t cap, int slots, cudaStream_t st) {
+  cap = (cap + 1023) / 1024 * 1024;
   if (c->g_lab && c->g_cap >= cap && c->g_slots >= slots) return GSOFA_OK;
   // the previous user of the slots must be done before they are replaced
   cudaEventSynchronize(c->g_done);
   cudaFree(c->g_lab);
   cudaFree(c->g_queue);
-  cudaFree(c->g_inq);
-  cudaFree(c->g_rowbits);
+  cudaFree(c->g_list);
+  cudaFree(c->g_bits);
   cudaFree(c->g_base);
-  c->g_lab = nullptr; c->g_queue = nullptr; c->g_inq = nullptr; c->g_rowbits = nullptr; c->g_base = nullptr;
+  c->g_lab = nullptr; c->g_queue = nullptr; c->g_list = nullptr; c->g_bits = nullptr; c->g_base = nullptr;
   c->g_cap = 0; c->g_slots = 0;
-  const int64_t capW = (cap + 31) / 32;
+  const int64_t capW = cap / 32, capS = capW / 32;
+  const size_t bits_words = (size_t)(2 * capW + 2 * capS) * (size_t)slots;
   if (cudaMalloc(&c->g_lab, sizeof(uint32_t) * cap * slots) != cudaSuccess ||
       cudaMalloc(&c->g_queue, sizeof(int32_t) * 2 * cap * slots) != cudaSuccess ||
-      cudaMalloc(&c->g_inq, sizeof(uint32_t) * capW * slots) != cudaSuccess ||
-      cudaMalloc(&c->g_rowbits, sizeof(uint32_t) * capW * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_list, sizeof(int32_t) * cap * slots) != cudaSuccess ||
+      cudaMalloc(&c->g_bits, sizeof(uint32_t) * bits_words) != cudaSuccess ||
       cudaMalloc(&c->g_base, sizeof(uint32_t) * slots) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(c->g_lab); cudaFree(c->g_queue); cudaFree(c->g_inq); cudaFree(c->g_rowbits); cudaFree(c->g_base);
-    c->g_lab = nullptr; c->g_queue = nullptr; c->g_inq = nullptr; c->g_rowbits = nullptr; c->g_base = nullptr;
+    cudaFree(c->g_lab); cudaFree(c->g_queue); cudaFree(c->g_list); cudaFree(c->g_bits); cudaFree(c->g_base);
+    c->g_lab = nullptr; c->g_queue = nullptr; c->g_list = nullptr; c->g_bits = nullptr; c->g_base = nullptr;
     return GSOFA_E_NOMEM;
   }
   cudaMemsetAsync(c->g_lab, 0xFF, sizeof(uint32_t) * cap * slots, st);
-  cudaMemsetAsync(c->g_inq, 0, sizeof(uint32_t) * capW * slots, st);
-  cudaMemsetAsync(c->g_rowbits, 0, sizeof(uint32_t) * capW * slots, st);
+  cudaMemsetAsync(c->g_bits, 0, sizeof(uint32_t) * bits_words, st);
   cudaMemsetAsync(c->g_base, 0xFF, sizeof(uint32_t) * slots, st);
   c->g_cap = cap;
   c->g_slots = slots;
@@ -327,11 +331,16 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     if (o.max_ctas > 0 && o.max_ctas < p->smem_grid) p->smem_grid = o.max_ctas;
   }
   if (S < n) {
-    int block = o.threads_per_source > 0 ? o.threads_per_source : 512;
-    p->glob_block = block;
-    int slots = o.max_concurrent > 0 ? o.max_concurrent : c->sms;
-    if (o.max_ctas > 0 && o.max_ctas < slots) slots = o.max_ctas;
-    p->glob_grid = slots;
+    // one warp per source; as many warps as 32 per SM, within the memory budget
+    const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
+    const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes / 2 : ((int64_t)16 << 30);
+    int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * 32;
+    const int64_t fit = budget / slot_bytes(cap);
+    if (slots > fit) slots = fit;
+    if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * 16) slots = (int64_t)o.max_ctas * 16;
+    if (slots < 1) return GSOFA_E_NOMEM;
+    p->glob_block = 512;
+    p->glob_grid = (int)slots;  // slots (warps); the launch uses ceil(slots / 16) CTAs
   }
   return GSOFA_OK;
 }
@@ -444,15 +453,6 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   if (plan.S < n) {
     glk.lock();
     have_global_lock = true;
-    if (o.mem_budget_bytes > 0) {
-      const long long per_slot = 12LL * n + 8LL * ((n + 31) / 32);
-      const long long need = per_slot * plan.glob_grid + 4LL * pool_cap + 24LL * n;
-      if (need > o.mem_budget_bytes) {
-        long long slots = (o.mem_budget_bytes - 4LL * pool_cap - 24LL * n) / per_slot;
-        if (slots < 1) { rc = GSOFA_E_NOMEM; goto fail; }
-        plan.glob_grid = (int)slots;
-      }
-    }
     rc = ensure_slots(c, n, plan.glob_grid, st);
     if (rc) goto fail;
     CK(cudaStreamWaitEvent(st, c->g_done, 0));
@@ -484,13 +484,20 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     if (plan.S < n) {
       a.order = order + plan.S;
       a.nsrc = n - plan.S;
-      a.g_lab = c->g_lab;
-      a.g_queue = c->g_queue;
-      a.g_inq = c->g_inq;
-      a.g_rowbits = c->g_rowbits;
-      a.g_base = c->g_base;
-      a.g_cap = c->g_cap;
-      LK(launch_trav_global(a, plan.glob_grid, plan.glob_block, st));
+      {
+        const int64_t capW = c->g_cap / 32, capS = capW / 32, slots = c->g_slots;
+        a.g_lab = c->g_lab;
+        a.g_queue = c->g_queue;
+        a.g_list = c->g_list;
+        a.g_P = c->g_bits;
+        a.g_U = c->g_bits + capW * slots;
+        a.g_PS = c->g_bits + 2 * capW * slots;
+        a.g_US = c->g_bits + 2 * capW * slots + capS * slots;
+        a.g_base = c->g_base;
+        a.g_cap = c->g_cap;
+        a.g_slots = plan.glob_grid;
+      }
+      LK(launch_trav_global(a, (plan.glob_grid + 15) / 16, plan.glob_block, st));
       CK(cudaEventRecord(c->g_done, st));
     }
     ev.rec(3, st);
@@ -786,10 +793,13 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.nmats = p.B;
   a.chunk = p.shape.work_chunk;
   a.mat_tot = p.mat_tot();
-  // external records become event nodes when this sequence is captured into a graph
-  if (t0 && (e = cudaEventRecordWithFlags(t0, st, cudaEventRecordExternal)) != cudaSuccess) return e;
+  // while capturing, external records become event nodes of the graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  const unsigned rf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (t0 && (e = cudaEventRecordWithFlags(t0, st, rf)) != cudaSuccess) return e;
   if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) return e;
-  if (t1 && (e = cudaEventRecordWithFlags(t1, st, cudaEventRecordExternal)) != cudaSuccess) return e;
+  if (t1 && (e = cudaEventRecordWithFlags(t1, st, rf)) != cudaSuccess) return e;
   if ((e = launch_supernode_batch(p.d_mats, p.B, p.chunks, o.chunk_size, p.pool, p.row_off, p.row_nL, p.row_nU,
                                   p.flags, p.mat_nsuper(), p.ctr(), st)) != cudaSuccess)
     return e;

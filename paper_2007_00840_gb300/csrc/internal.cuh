@@ -82,13 +82,17 @@ struct TravArgs {
   int32_t nmats;
   int32_t chunk;                      // work items taken per fetch (>= 1)
   unsigned long long* mat_tot;        // per matrix: [sum nnz(L(i,:)), sum nnz(U(i,:))]
-  // global tier: per-slot working arrays (slot = CTA index)
-  uint32_t* g_lab;                    // slots x n (epoch-encoded maxId)
-  int32_t* g_queue;                   // slots x 2n (current / next frontier)
-  uint32_t* g_inq;                    // slots x ceil(n/32) (dedup of the next frontier)
-  uint32_t* g_rowbits;                // slots x ceil(n/32) (columns of the row found so far)
+  // global tier: per-slot working arrays (slot = warp)
+  uint32_t* g_lab;                    // slots x cap (epoch-encoded maxId)
+  int32_t* g_queue;                   // slots x 2cap (current / next class frontier)
+  int32_t* g_list;                    // slots x cap (the row's L columns, in order)
+  uint32_t* g_P;                      // slots x capW (pending fills, by id)
+  uint32_t* g_PS;                     // slots x capS (summary: bit per nonzero P word)
+  uint32_t* g_U;                      // slots x capW (U columns)
+  uint32_t* g_US;                     // slots x capS (summary of U)
   uint32_t* g_base;                   // per slot: current maxId window base (persists across launches)
-  int64_t g_cap;                      // per-slot capacity in vertices (>= n)
+  int64_t g_cap;                      // per-slot capacity in vertices (>= n, multiple of 1024)
+  int32_t g_slots;                    // number of slots (warps) of the launch
 };
 
 // ---- launchers (return cudaGetLastError())
@@ -97,7 +101,6 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16);
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st);
 int trav_smem_static_bytes();
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16);
-size_t trav_global_smem_bytes(int32_t n);
 cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st);
 
 cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,

@@ -1,297 +1,308 @@
-// Multi-source maxId traversal, global-memory tier (Section 4, Fig. 5).
+// Multi-source maxId traversal, global-memory tier (Section 4, Fig. 5), with
+// the frontier processed in maxId-class order.
 //
-// Used for sources whose maxId array does not fit in shared memory.  The rule
-// is the same as in traverse_smem.cu; the data placement differs:
-//   g_lab      per-slot maxId array in HBM (slot = CTA), encoded with the
-//              value-range windows of Section 4; the window base persists per
-//              slot across sources and launches (g_base), so the array is only
-//              refilled when the 32-bit range is used up;
-//   g_queue    current / next frontier as compact queues (a frontier holds at
-//              most s distinct vertices), deduplicated with the g_inq bitmap;
-//   g_rowbits  the columns of row s found so far (L fills and U entries) as a
-//              bitmap over [0, n), with a one-bit-per-word summary in shared
-//              memory so emission visits only nonzero words, in order.
-// Bubble removal (Section 6): vertices above the source keep no maxId.
+// Used when a source's maxId array does not fit in shared memory.  One warp
+// owns one source at a time (persistent warps, work counter in global memory);
+// each warp has a slot of global memory with
+//   lab      the maxId array, encoded with the value-range windows of Section 4
+//            (the window base persists per slot across sources and launches);
+//   P, PS    pending frontier vertices as a bitmap over [0, s) plus a summary
+//            with one bit per nonzero P word;
+//   U, US    the U part of the row as a bitmap plus its summary;
+//   queue    the frontier of the class being expanded; list: the L columns.
+//
+// Frontier order.  A frontier vertex f proposes nm = max(maxId(f), f) to its
+// neighbours (the relaxation of Section 4).  On large graphs with long paths
+// (nested-dissection orderings, whose separators carry consecutive ids)
+// breadth-first order lowers the same maxId many times (tens of expansions per
+// vertex).  Here the frontier is expanded by increasing proposal, one class of
+// equal proposals at a time (label-bucketed frontier processing with bucket
+// width 1, cf. the comparison with Dijkstra's algorithm in Section 8).  In that
+// order a maxId is set once, when a vertex is first reached, and a vertex
+// reached from class p with id w > p is a fill whose proposal is its own id w;
+// so the deferred part of the frontier is exactly the set of pending fills,
+// kept as the bitmap P and taken in increasing order.  Class p is the pending
+// fill p together with the vertices below p it reaches through unreached
+// vertices below p, all expanded in parallel breadth-first levels.  The L row
+// is the sequence of classes (sorted by construction); the U row comes from
+// the U bitmap.
 #include "internal.cuh"
 
 namespace gsofa {
 
 namespace {
 
-constexpr int BIG_DEG = 32;
-constexpr int BATCH = 8;  // column loads issued together per frontier vertex
-
-struct GState {
+struct Slot {
   uint32_t* lab;
-  uint32_t* inq;
-  uint32_t* rowbits;
-  uint32_t* summ;
-  int32_t* qnext;
-  int* qn;         // shared counter of qnext
-  uint32_t base;
-  int32_t s;
-  int32_t n;
-  int32_t fill_first;
+  int32_t* qa;
+  int32_t* qb;
+  int32_t* list;
+  uint32_t* P;
+  uint32_t* PS;
+  uint32_t* U;
+  uint32_t* US;
 };
 
-__device__ __forceinline__ void set_rowbit(const GState& g, int w) {
-  const uint32_t bit = 1u << (w & 31);
-  uint32_t* p = &g.rowbits[w >> 5];
+__device__ __forceinline__ void set_bit2(uint32_t* W, uint32_t* S, int v) {
+  const uint32_t bit = 1u << (v & 31);
+  uint32_t* p = &W[v >> 5];
   if (*(volatile uint32_t*)p & bit) return;
   const uint32_t old = atomicOr(p, bit);
-  if (old == 0u) atomicOr(&g.summ[w >> 10], 1u << ((w >> 5) & 31));
+  if (old == 0u) atomicOr(&S[v >> 10], 1u << ((v >> 5) & 31));
 }
 
-__device__ __forceinline__ void enqueue(const GState& g, int w) {
-  const uint32_t bit = 1u << (w & 31);
-  const uint32_t old = atomicOr(&g.inq[w >> 5], bit);
-  if (!(old & bit)) {
-    const int pos = atomicAdd(g.qn, 1);
-    g.qnext[pos] = w;
+// Smallest set bit of P at a position in [from, s); -1 if none.  Warp-wide.
+__device__ int next_pending(const Slot& sl, int from, int s, int lane) {
+  if (from >= s) return -1;
+  const int w0 = from >> 5;
+  const uint32_t first = *(volatile uint32_t*)&sl.P[w0] & (0xFFFFFFFFu << (from & 31));
+  if (first) {
+    const int v = (w0 << 5) + __ffs(first) - 1;
+    return v < s ? v : -1;
   }
-}
-
-__device__ __forceinline__ void relax_g(const GState& g, int w, uint32_t nmE, int* bad) {
-  if ((unsigned)w >= (unsigned)g.n) { *bad = 1; return; }
-  if (w < g.s) {
-    const uint32_t wE = g.base + 1u + (uint32_t)w;
-    if (g.fill_first && *(volatile uint32_t*)&g.lab[w] < wE) return;
-    const uint32_t old = atomicMin(&g.lab[w], nmE);
-    if (nmE < old) {
-      if (nmE < wE && old >= wE) set_rowbit(g, w);   // w just became a fill of L(s,:)
-      if (old > wE) enqueue(g, w);                   // w's own proposal changed
+  // summary search from P word w0 + 1
+  const int wstart = w0 + 1;
+  const int nw = (s + 31) >> 5;
+  for (int sw0 = wstart >> 5; (sw0 << 5) < nw; sw0 += 32) {
+    const int sw = sw0 + lane;
+    uint32_t m = 0u;
+    if ((sw << 5) < nw) {
+      m = *(volatile uint32_t*)&sl.PS[sw];
+      if (sw == (wstart >> 5)) m &= 0xFFFFFFFFu << (wstart & 31);
     }
-  } else if (w > g.s) {
-    set_rowbit(g, w);
+    const unsigned any = __ballot_sync(FULL, m != 0u);
+    if (any) {
+      const int l = __ffs(any) - 1;
+      const uint32_t ml = __shfl_sync(FULL, m, l);
+      const int pw = ((sw0 + l) << 5) + __ffs(ml) - 1;  // P word index
+      const uint32_t word = *(volatile uint32_t*)&sl.P[pw];
+      const int v = (pw << 5) + __ffs(word) - 1;
+      return (word != 0u && v < s) ? v : -1;
+    }
   }
+  return -1;
+}
+
+// Relax edge (. -> w) for class t of source s with encoded proposal pE.
+// Returns 1 when w joins class t.
+__device__ __forceinline__ int relax_class(const Slot& sl, int w, int s, int t, uint32_t pE, int n, int* bad) {
+  if ((unsigned)w >= (unsigned)n) { *bad = 1; return 0; }
+  if (w > s) { set_bit2(sl.U, sl.US, w); return 0; }
+  if (w == s) return 0;
+  const uint32_t old = atomicMin(&sl.lab[w], pE);
+  if (old > pE) {                       // first reached, now with maxId t
+    if (w < t) return 1;                // same class
+    set_bit2(sl.P, sl.PS, w);           // a fill of L(s,:); its own class later
+  }
+  return 0;
 }
 
 }  // namespace
 
-size_t trav_global_smem_bytes(int32_t n) {
-  const size_t NW = ((size_t)n + 31) / 32;
-  return 4 * ((NW + 31) / 32);
-}
-
-__global__ void __launch_bounds__(1024, 1) trav_global_kernel(TravArgs a) {
-  extern __shared__ uint32_t summ[];
+__global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int slot = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (slot >= a.g_slots) return;
   const int n = a.n;
-  const int NW = (n + 31) >> 5, NSW = (NW + 31) >> 5;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nthr = blockDim.x, nwarps = nthr >> 5;
-  const size_t slot = blockIdx.x;
-  const size_t cap = (size_t)a.g_cap, capW = (cap + 31) / 32;
-  uint32_t* lab = a.g_lab + slot * cap;
-  int32_t* qA = a.g_queue + slot * 2 * cap;
-  int32_t* qB = qA + cap;
-  uint32_t* inq = a.g_inq + slot * capW;
-  uint32_t* rowbits = a.g_rowbits + slot * capW;
+  const size_t cap = (size_t)a.g_cap, capW = cap / 32, capS = capW / 32;
+  Slot sl;
+  sl.lab = a.g_lab + (size_t)slot * cap;
+  sl.qa = a.g_queue + (size_t)slot * 2 * cap;
+  sl.qb = sl.qa + cap;
+  sl.list = a.g_list + (size_t)slot * cap;
+  sl.P = a.g_P + (size_t)slot * capW;
+  sl.PS = a.g_PS + (size_t)slot * capS;
+  sl.U = a.g_U + (size_t)slot * capW;
+  sl.US = a.g_US + (size_t)slot * capS;
+  const unsigned lt = (1u << lane) - 1u;
 
-  __shared__ int s_src, s_diag;
-  __shared__ int s_q[3];
-  __shared__ int s_wc[32][2];
-  __shared__ long long s_off;
-  __shared__ int s_nL;
-  __shared__ uint32_t s_base;
-
-  for (int i = tid; i < NSW; i += nthr) summ[i] = 0u;
-  const uint32_t span = (uint32_t)n + 2u;
-  if (tid == 0) s_base = a.g_base[slot];
+  uint32_t base = a.g_base[slot];
   unsigned long long n_exp = 0, n_edge = 0;
   int bad = 0;
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) {
+    int s = -1;
+    if (lane == 0) {
       const int k = atomicAdd(&a.ctr->work_global, 1);
-      s_src = (k < a.nsrc && !input_error(a.ctr)) ? a.order[k] : -1;
-      s_diag = 0;
-      s_q[0] = s_q[1] = s_q[2] = 0;
+      if (k < a.nsrc && !input_error(a.ctr)) s = a.order ? a.order[k] : a.nsrc - 1 - k;
     }
-    __syncthreads();
-    const int s = s_src;
+    s = __shfl_sync(FULL, s, 0);
     if (s < 0) break;
 
-    // next maxId window; refill the slot when the 32-bit range is used up
-    uint32_t base = s_base;
+    // maxId window of this source (values base+1+l for l in [-1, s))
+    const uint32_t span = (uint32_t)s + 1u;
     if (base >= span) {
       base -= span;
     } else {
-      for (size_t i = tid; i < cap; i += nthr) lab[i] = 0xFFFFFFFFu;
+      for (size_t i = lane; i < cap; i += 32) sl.lab[i] = 0xFFFFFFFFu;
       base = 0xFFFFFFFFu - span;
+      __syncwarp();
     }
-    __syncthreads();  // everyone has read s_base (and the refill is done)
-    if (tid == 0) s_base = base;
 
-    GState g{lab, inq, rowbits, summ, qA, &s_q[0], base, s, n, a.fill_first};
-
-    const int rb = a.rowptr[s], re = a.rowptr[s + 1];
-    for (int e = rb + tid; e < re; e += nthr) {
-      const int w = a.colidx[e];
+    // seed: neighbours below s are pending fills with maxId -1; above s, U entries
+    const int rb = __ldg(a.rowptr + s), re = __ldg(a.rowptr + s + 1);
+    int diag = 0;
+    for (int e = rb + lane; e < re; e += 32) {
+      const int w = __ldg(a.colidx + e);
       if ((unsigned)w >= (unsigned)n) { bad = 1; continue; }
       if (w < s) {
-        lab[w] = base;          // encoded -1: no intermediate vertex
-        set_rowbit(g, w);
-        enqueue(g, w);
+        sl.lab[w] = base;
+        set_bit2(sl.P, sl.PS, w);
       } else if (w > s) {
-        set_rowbit(g, w);
+        set_bit2(sl.U, sl.US, w);
       } else {
-        s_diag = 1;
+        diag = 1;
       }
     }
-    __syncthreads();
+    diag = __any_sync(FULL, diag);
+    __syncwarp();
 
-    int32_t* qcur = qA;
-    int32_t* qnxt = qB;
-    int qlen = s_q[0];
-    // same bound as the shared tier: labels are final after s+1 levels
-    const long long cap_lv = (long long)s + 3;
-    long long level = 0;
-    while (qlen > 0) {
-      level++;
-      const int li = (int)(level % 3);
-      if (tid == 0) s_q[(li + 1) % 3] = 0;
-      g.qnext = qnxt;
-      g.qn = &s_q[li];
-      // From here on a dedup bit means "already in the next frontier": clear the
-      // bits of the current frontier before any expansion of this level, so a
-      // vertex whose maxId drops while it is being expanded is queued again.
-      for (int i = tid; i < qlen; i += nthr) {
-        const int v = qcur[i];
-        atomicAnd(&inq[v >> 5], ~(1u << (v & 31)));
+    // sweep the pending fills in increasing order; each starts one class
+    int nL = 0;
+    int cursor = 0;
+    for (;;) {
+      const int t = next_pending(sl, cursor, s, lane);
+      if (t < 0) break;
+      cursor = t + 1;
+      if (lane == 0) {
+        const uint32_t bit = 1u << (t & 31);
+        const uint32_t old = atomicAnd(&sl.P[t >> 5], ~bit);
+        if ((old & ~bit) == 0u) atomicAnd(&sl.PS[t >> 10], ~(1u << ((t >> 5) & 31)));
+        sl.list[nL] = t;  // t is a fill of L(s,:)
       }
-      __syncthreads();
-      for (int i0 = warp * 32; i0 < qlen; i0 += nthr) {
-        const int i = i0 + lane;
-        int v = -1, eb = 0, ee = 0;
-        uint32_t nmE = 0u;
-        if (i < qlen) {
-          v = qcur[i];
-          eb = __ldg(a.rowptr + v);
-          ee = __ldg(a.rowptr + v + 1);
-          const uint32_t lv = *(volatile uint32_t*)&lab[v];
-          const uint32_t vE = base + 1u + (uint32_t)v;
-          nmE = lv > vE ? lv : vE;
-          n_exp++;
-          if (ee - eb <= BIG_DEG) {
-            n_edge += (unsigned long long)(ee - eb);
-            for (int e0 = eb; e0 < ee; e0 += BATCH) {
-              int wv[BATCH];  // independent loads first, then the relaxations
-#pragma unroll
-              for (int q = 0; q < BATCH; q++) wv[q] = (e0 + q < ee) ? __ldg(a.colidx + e0 + q) : 0;
-#pragma unroll
-              for (int q = 0; q < BATCH; q++)
-                if (e0 + q < ee) relax_g(g, wv[q], nmE, &bad);
+      nL++;
+      const uint32_t pE = base + 1u + (uint32_t)t;  // encoded class value (proposal) t
+      // class t: breadth-first over unreached vertices below t; the first level is t alone
+      int32_t* qc = sl.qa;
+      int32_t* qn = sl.qb;
+      int qlen = 1;
+      bool single = true;
+      while (qlen > 0) {
+        int nq = 0;
+        if (single) {  // one vertex: the lanes share its row
+          const int eb = __ldg(a.rowptr + t), ee = __ldg(a.rowptr + t + 1);
+          if (lane == 0) { n_exp++; n_edge += (unsigned long long)(ee - eb); }
+          for (int e0 = eb; e0 < ee; e0 += 32) {
+            const int e = e0 + lane;
+            int w = 0, enq = 0;
+            if (e < ee) {
+              w = __ldg(a.colidx + e);
+              enq = relax_class(sl, w, s, t, pE, n, &bad);
+            }
+            const unsigned m = __ballot_sync(FULL, enq);
+            if (enq) qn[nq + __popc(m & lt)] = w;
+            nq += __popc(m);
+          }
+          single = false;
+        } else {  // several: one vertex per lane
+          for (int i0 = 0; i0 < qlen; i0 += 32) {
+            const int i = i0 + lane;
+            int eb = 0, ee = 0;
+            if (i < qlen) {
+              const int v = qc[i];
+              eb = __ldg(a.rowptr + v);
+              ee = __ldg(a.rowptr + v + 1);
+              n_exp++;
+              n_edge += (unsigned long long)(ee - eb);
+            }
+            const int maxdeg = __reduce_max_sync(FULL, ee - eb);
+            for (int k = 0; k < maxdeg; k++) {
+              int w = 0, enq = 0;
+              if (eb + k < ee) {
+                w = __ldg(a.colidx + eb + k);
+                enq = relax_class(sl, w, s, t, pE, n, &bad);
+              }
+              const unsigned m = __ballot_sync(FULL, enq);
+              if (enq) qn[nq + __popc(m & lt)] = w;
+              nq += __popc(m);
             }
           }
         }
-        unsigned bigm = __ballot_sync(FULL, v >= 0 && (ee - eb) > BIG_DEG);
-        while (bigm) {
-          const int l = __ffs(bigm) - 1;
-          bigm &= bigm - 1;
-          const int beb = __shfl_sync(FULL, eb, l), bee = __shfl_sync(FULL, ee, l);
-          const uint32_t bnm = __shfl_sync(FULL, nmE, l);
-          if (lane == 0) n_edge += (unsigned long long)(bee - beb);
-          for (int e = beb + lane; e < bee; e += 32) relax_g(g, __ldg(a.colidx + e), bnm, &bad);
-        }
-      }
-      __syncthreads();
-      qlen = s_q[li];
-      int32_t* t = qcur;
-      qcur = qnxt;
-      qnxt = t;
-      if (level >= cap_lv && qlen > 0) {
-        // never expected: drop the frontier, leave the slot clean, flag it
-        for (int i = tid; i < qlen; i += nthr) {
-          const int v = qcur[i];
-          atomicAnd(&inq[v >> 5], ~(1u << (v & 31)));
-        }
-        if (tid == 0) atomicOr(&a.ctr->err, ERR_NOCONV);
-        __syncthreads();
-        break;
+        __syncwarp();
+        int32_t* tq = qc;
+        qc = qn;
+        qn = tq;
+        qlen = nq;
       }
     }
 
-    // ---- emission: walk the summary in order; thread t owns a contiguous range
-    const int per = (NSW + nthr - 1) / nthr;
-    const int lo = tid * per, hi = min(NSW, lo + per);
-    int cL = 0, cU = 0;
-    for (int sw = lo; sw < hi; sw++) {
-      uint32_t m = summ[sw];
-      while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const int fw = (sw << 5) + j;
-        const uint32_t word = rowbits[fw];
-        const int wb = fw << 5;
-        if (wb + 31 < s) cL += __popc(word);
-        else if (wb > s) cU += __popc(word);
-        else {
-          const int k = s - wb;  // bit of s inside this word (never set)
-          const uint32_t lowm = (k == 0) ? 0u : (0xFFFFFFFFu >> (32 - k));
-          cL += __popc(word & lowm);
-          cU += __popc(word & ~lowm);
-        }
-      }
-    }
-    // block-wide exclusive scan of (cL, cU) in thread order
-    int iL = cL, iU = cU;
+    // ---- emission: count U through its summary, take a pool offset, write the row
+    const int nw = (n + 31) >> 5;
+    const int ns = (nw + 31) >> 5;
+    const int s_lo = (s + 1) >> 10;  // first summary word that can hold a column > s
+    int nU = 1;
+    for (int sw0 = s_lo; sw0 < ns; sw0 += 32) {
+      const int sw = sw0 + lane;
+      const uint32_t m = sw < ns ? sl.US[sw] : 0u;
+      unsigned any = __ballot_sync(FULL, m != 0u);
+      while (any) {
+        const int l = __ffs(any) - 1;
+        any &= any - 1;
+        const uint32_t ml = __shfl_sync(FULL, m, l);
+        const int pw = ((sw0 + l) << 5) + lane;
+        const uint32_t word = ((ml >> lane) & 1u) ? sl.U[pw] : 0u;
+        int c = __popc(word);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int tL = __shfl_up_sync(FULL, iL, o), tU = __shfl_up_sync(FULL, iU, o);
-      if (lane >= o) { iL += tL; iU += tU; }
-    }
-    if (lane == 31) { s_wc[warp][0] = iL; s_wc[warp][1] = iU; }
-    __syncthreads();
-    if (tid == 0) {
-      int tl = 0, tu = 0;
-      for (int w = 0; w < nwarps; w++) {
-        const int x = s_wc[w][0]; s_wc[w][0] = tl; tl += x;
-        const int y = s_wc[w][1]; s_wc[w][1] = tu; tu += y;
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        nU += c;
       }
-      const int nL = tl, nU = tu + 1;
-      const unsigned long long off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
-      const bool ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
-      s_off = ok ? (long long)off : -1LL;
-      s_nL = nL;
+    }
+    unsigned long long off = 0ull;
+    int ok = 0;
+    if (lane == 0) {
+      off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
+      ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
       a.row_off[s] = ok ? (int64_t)off : -1;
       a.row_nL[s] = nL;
       a.row_nU[s] = nU;
-      a.fill_count[s] = nL + nU - ((re - rb) + (s_diag ? 0 : 1));
+      a.fill_count[s] = nL + nU - ((re - rb) + (diag ? 0 : 1));
       atomicAdd(&a.ctr->total_L, (unsigned long long)nL);
       atomicAdd(&a.ctr->total_U, (unsigned long long)nU);
       if (ok) a.pool[off + nL] = (uint32_t)s;
       else atomicOr(&a.ctr->err, ERR_OVERFLOW);
     }
-    __syncthreads();
-    const long long off = s_off;
-    const int nL = s_nL;
-    long long pL = off + s_wc[warp][0] + (iL - cL);
-    long long pU = off + nL + 1 + s_wc[warp][1] + (iU - cU);
-    for (int sw = lo; sw < hi; sw++) {
-      uint32_t m = summ[sw];
-      while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const int fw = (sw << 5) + j;
-        uint32_t word = rowbits[fw];
-        rowbits[fw] = 0u;
-        if (off >= 0) {
+    off = __shfl_sync(FULL, off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    if (ok)
+      for (int i = lane; i < nL; i += 32) a.pool[off + i] = (uint32_t)sl.list[i];
+    long long pos = (long long)off + nL + 1;
+    for (int sw0 = s_lo; sw0 < ns; sw0 += 32) {
+      const int sw = sw0 + lane;
+      const uint32_t m = sw < ns ? sl.US[sw] : 0u;
+      unsigned any = __ballot_sync(FULL, m != 0u);
+      while (any) {
+        const int l = __ffs(any) - 1;
+        any &= any - 1;
+        const uint32_t ml = __shfl_sync(FULL, m, l);
+        const int pw = ((sw0 + l) << 5) + lane;
+        uint32_t word = 0u;
+        if ((ml >> lane) & 1u) {
+          word = sl.U[pw];
+          sl.U[pw] = 0u;
+        }
+        const int c = __popc(word);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int tt = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += tt;
+        }
+        if (ok) {
+          long long p = pos + (inc - c);
           while (word) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
-            const int col = (fw << 5) + b;
-            if (col < s) a.pool[pL++] = (uint32_t)col;
-            else a.pool[pU++] = (uint32_t)col;
+            a.pool[p++] = (uint32_t)((pw << 5) + b);
           }
         }
+        pos += __shfl_sync(FULL, inc, 31);
       }
-      summ[sw] = 0u;
+      if (sw < ns && m) sl.US[sw] = 0u;
     }
+    __syncwarp();
   }
 
-  __syncthreads();
-  if (tid == 0) a.g_base[slot] = s_base;
+  if (lane == 0) a.g_base[slot] = base;
   if (bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
   if (a.collect_stats) {
 #pragma unroll
@@ -307,11 +318,7 @@ __global__ void __launch_bounds__(1024, 1) trav_global_kernel(TravArgs a) {
 }
 
 cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st) {
-  const size_t bytes = trav_global_smem_bytes(a.n);
-  cudaError_t e = cudaFuncSetAttribute(trav_global_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(bytes > 0 ? bytes : 4));
-  if (e != cudaSuccess) return e;
-  trav_global_kernel<<<grid, block, bytes > 0 ? bytes : 4, st>>>(a);
+  trav_global_kernel<<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 
