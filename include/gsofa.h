@@ -69,7 +69,10 @@ typedef struct gsofa_options {
     int32_t list_capacity;       /* frontier list entries kept in shared memory (default: as many as fit) */
     int32_t max_ctas;            /* cap on traversal CTAs per launch, so concurrent launches share the GPU
                                     (default 0: one full wave) */
-    int32_t reserved[3];
+    int32_t frontier_order;      /* 0: automatic; 1: breadth-first levels (shared-memory tier wherever the
+                                    maxId array fits on chip); 2: by increasing maxId class (warp tier).
+                                    Same result; with autotune = 1 the faster one is kept per shape */
+    int32_t reserved[2];
 } gsofa_options;
 
 /* Per-call statistics (filled when options.collect_stats == 1). */
@@ -175,16 +178,17 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
  * Requests are admitted in arrival order while their projected device memory
  * (CSR copy, per-row workspace, row pool and outputs, label slots of large
  * orders) fits under mem_cap_bytes; each of `streams` slots runs the admitted
- * requests waiting at that moment (up to max_batch) as one multi-matrix batch,
- * and the batches of different slots overlap on the GPU (each limited to
- * opts.max_ctas traversal CTAs; 0 = 4 x SMs / streams).
+ * requests waiting at that moment (up to max_batch) as one multi-matrix batch.
+ * A slot launches as soon as it is free, so the next batch queues on the GPU
+ * behind the running one and their phases overlap (opts.max_ctas can split
+ * the GPU between slots instead).
  */
 typedef struct gsofa_server gsofa_server;
 
 typedef struct gsofa_server_config {
     int64_t mem_cap_bytes;       /* admission cap on projected device memory (default 150 GiB) */
     int32_t max_inflight;        /* admitted, unfinished requests at most (default 8192) */
-    int32_t streams;             /* concurrent batch slots (default 3, at most 16) */
+    int32_t streams;             /* concurrent batch slots (default 2, at most 16) */
     int32_t max_batch;           /* requests per batch launch (default 512) */
     int32_t queue_capacity;      /* pending requests before submit returns GSOFA_E_BUSY (default 2^20) */
     gsofa_options opts;          /* options of every batch */

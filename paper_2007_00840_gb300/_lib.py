@@ -34,7 +34,8 @@ class gsofa_options(ctypes.Structure):
         ("work_chunk", ctypes.c_int32),
         ("list_capacity", ctypes.c_int32),
         ("max_ctas", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("frontier_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

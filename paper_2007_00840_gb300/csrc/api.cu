@@ -45,6 +45,8 @@ struct Ctx {
   // row-pool size that fitted last time, by matrix order
   std::mutex hmu;
   std::map<int32_t, long long> pool_hint;
+  // single-matrix autotune: faster frontier order by (n, nnz)
+  std::map<std::pair<int32_t, int64_t>, int> order_tuned;
 };
 
 std::mutex g_ctx_mu;
@@ -313,7 +315,7 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
   int32_t S = trav_smem_max_S(n, limit, label16);
   if (o.smem_max_source > 0 && o.smem_max_source < S) S = o.smem_max_source;
-  if (o.smem_max_source < 0) S = 0;  // every source in the global tier
+  if (o.smem_max_source < 0 || o.frontier_order == 2) S = 0;  // every source in the class-ordered tier
   if (S > n) S = n;
   if (S < 0) S = 0;
   p->S = S;
@@ -361,8 +363,9 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->max_concurrent = in->max_concurrent;
   o->mem_budget_bytes = in->mem_budget_bytes;
   if (in->work_chunk < 0 || in->list_capacity < 0) return GSOFA_E_INVAL;
-  if (in->max_ctas < 0) return GSOFA_E_INVAL;
+  if (in->max_ctas < 0 || in->frontier_order < 0 || in->frontier_order > 2) return GSOFA_E_INVAL;
   o->max_ctas = in->max_ctas;
+  o->frontier_order = in->frontier_order;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -621,6 +624,8 @@ struct LaunchShape {
   int occ = 1;
   int32_t list_cap = 1024;
   int work_chunk = 1;
+  int kernel = 0;   // 0: shared-memory breadth-first tier; 1: class-ordered warp tier
+  int slots = 0;    // kernel 1: warps (sources in flight)
 };
 
 // Workspace and captured graph of one batch signature.
@@ -651,6 +656,14 @@ struct BatchPlan {
   int32_t* spill = nullptr;
   int64_t spill_cap = 0;
   int64_t spill_alloc = 0;
+  // class-ordered tier slots (kernel 1)
+  uint32_t* c_lab = nullptr;
+  int32_t* c_queue = nullptr;
+  int32_t* c_list = nullptr;
+  uint32_t* c_bits = nullptr;
+  uint32_t* c_base = nullptr;
+  int64_t c_cap = 0;
+  int c_slots = 0;
   int grid = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -668,7 +681,8 @@ void free_plan(BatchPlan* p) {
   if (p->transient) {
     for (void* q : {(void*)p->d_mats, (void*)p->d_item_start, (void*)p->d_mat_order, (void*)p->d_ctr,
                     (void*)p->row_off, (void*)p->row_nL, (void*)p->row_nU, (void*)p->flags, (void*)p->fill,
-                    (void*)p->pool, (void*)p->spill})
+                    (void*)p->pool, (void*)p->spill, (void*)p->c_lab, (void*)p->c_queue, (void*)p->c_list,
+                    (void*)p->c_bits, (void*)p->c_base})
       if (q) cudaFreeAsync(q, p->stream);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -689,6 +703,11 @@ void free_plan(BatchPlan* p) {
   cudaFree(p->fill);
   cudaFree(p->pool);
   cudaFree(p->spill);
+  cudaFree(p->c_lab);
+  cudaFree(p->c_queue);
+  cudaFree(p->c_list);
+  cudaFree(p->c_bits);
+  cudaFree(p->c_base);
   if (p->h_ctr) cudaFreeHost(p->h_ctr);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
@@ -742,11 +761,20 @@ void save_tune_entry(uint64_t key, const LaunchShape& sh) {
   std::fclose(fp);
 }
 
+// Warps of the class-ordered tier for orders up to n_max: per_sm per SM, within 8 GiB.
+int class_slots(Ctx* c, int32_t n_max, int per_sm) {
+  const int64_t cap = ((int64_t)n_max + 1023) / 1024 * 1024;
+  int64_t slots = (int64_t)c->sms * per_sm;
+  const int64_t fit = ((int64_t)8 << 30) / slot_bytes(cap);
+  if (slots > fit) slots = fit;
+  return (int)slots;
+}
+
 // Launch shapes worth timing for a batch whose largest order is n_max.
-std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, size_t limit) {
+std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, size_t limit, int order) {
   std::vector<LaunchShape> out;
   const int blocks[3] = {256, 512, 1024};
-  for (int b : blocks) {
+  for (int b : (order == 2 ? std::vector<int>{} : std::vector<int>{blocks[0], blocks[1], blocks[2]})) {
     int block = 0, occ = 0;
     int32_t cap = 0;
     if (choose_smem_config(c->sms, limit, n_max, n_max, label16, b, &block, &occ, &cap) != GSOFA_OK) continue;
@@ -759,6 +787,12 @@ std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, si
         out.push_back(sh);
       }
     }
+  }
+  for (int per_sm : (order == 1 ? std::vector<int>{} : std::vector<int>{16, 32})) {
+    LaunchShape sh;
+    sh.kernel = 1;
+    sh.slots = class_slots(c, n_max, per_sm);
+    if (sh.slots > 0) out.push_back(sh);
   }
   return out;
 }
@@ -798,7 +832,22 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   cudaStreamIsCapturing(st, &cs);
   const unsigned rf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (t0 && (e = cudaEventRecordWithFlags(t0, st, rf)) != cudaSuccess) return e;
-  if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) return e;
+  if (p.shape.kernel == 1) {
+    const int64_t capW = p.c_cap / 32, capS = capW / 32, ns = p.c_slots;
+    a.g_lab = p.c_lab;
+    a.g_queue = p.c_queue;
+    a.g_list = p.c_list;
+    a.g_P = p.c_bits;
+    a.g_U = p.c_bits + capW * ns;
+    a.g_PS = p.c_bits + 2 * capW * ns;
+    a.g_US = p.c_bits + 2 * capW * ns + capS * ns;
+    a.g_base = p.c_base;
+    a.g_cap = p.c_cap;
+    a.g_slots = p.shape.slots;
+    if ((e = launch_trav_global(a, (p.shape.slots + 15) / 16, 512, st)) != cudaSuccess) return e;
+  } else if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) {
+    return e;
+  }
   if (t1 && (e = cudaEventRecordWithFlags(t1, st, rf)) != cudaSuccess) return e;
   if ((e = launch_supernode_batch(p.d_mats, p.B, p.chunks, o.chunk_size, p.pool, p.row_off, p.row_nL, p.row_nU,
                                   p.flags, p.mat_nsuper(), p.ctr(), st)) != cudaSuccess)
@@ -810,6 +859,44 @@ int set_shape(Ctx* c, BatchPlan* p, const LaunchShape& sh) {
   p->shape = sh;
   p->grid = c->sms * sh.occ;
   if (p->max_ctas > 0 && p->max_ctas < p->grid) p->grid = p->max_ctas;
+  if (sh.kernel == 1) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    const int64_t cap = ((int64_t)p->n_max + 1023) / 1024 * 1024;
+    if (p->c_lab && p->c_cap >= cap && p->c_slots >= sh.slots) return GSOFA_OK;
+    for (void* q : {(void*)p->c_lab, (void*)p->c_queue, (void*)p->c_list, (void*)p->c_bits, (void*)p->c_base})
+      if (q) { if (p->transient) cudaFreeAsync(q, p->stream); else cudaFree(q); }
+    p->c_lab = nullptr; p->c_queue = nullptr; p->c_list = nullptr; p->c_bits = nullptr; p->c_base = nullptr;
+    const int64_t ns = sh.slots, capW = cap / 32, capS = capW / 32;
+    const size_t bits_words = (size_t)(2 * capW + 2 * capS) * (size_t)ns;
+    cudaStream_t ast = p->transient ? p->stream : p->cap_stream;
+    bool ok;
+    if (p->transient) {
+      ok = palloc(c, &p->c_lab, (size_t)(cap * ns), ast) == cudaSuccess &&
+           palloc(c, &p->c_queue, (size_t)(2 * cap * ns), ast) == cudaSuccess &&
+           palloc(c, &p->c_list, (size_t)(cap * ns), ast) == cudaSuccess &&
+           palloc(c, &p->c_bits, bits_words, ast) == cudaSuccess && palloc(c, &p->c_base, (size_t)ns, ast) == cudaSuccess;
+    } else {
+      ok = cudaMalloc(&p->c_lab, sizeof(uint32_t) * (size_t)(cap * ns)) == cudaSuccess &&
+           cudaMalloc(&p->c_queue, sizeof(int32_t) * (size_t)(2 * cap * ns)) == cudaSuccess &&
+           cudaMalloc(&p->c_list, sizeof(int32_t) * (size_t)(cap * ns)) == cudaSuccess &&
+           cudaMalloc(&p->c_bits, sizeof(uint32_t) * bits_words) == cudaSuccess &&
+           cudaMalloc(&p->c_base, sizeof(uint32_t) * (size_t)ns) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      return GSOFA_E_NOMEM;
+    }
+    cudaMemsetAsync(p->c_lab, 0xFF, sizeof(uint32_t) * (size_t)(cap * ns), ast);
+    cudaMemsetAsync(p->c_bits, 0, sizeof(uint32_t) * bits_words, ast);
+    cudaMemsetAsync(p->c_base, 0xFF, sizeof(uint32_t) * (size_t)ns, ast);
+    if (!p->transient) cudaStreamSynchronize(ast);
+    p->c_cap = cap;
+    p->c_slots = (int)ns;
+    return GSOFA_OK;
+  }
   // per CTA two overflow lists of (n_max - list capacity) entries
   p->spill_cap = p->n_max > sh.list_cap ? (int64_t)p->n_max - sh.list_cap : 1;
   const int64_t need = (int64_t)p->grid * 2 * p->spill_cap;
@@ -979,7 +1066,7 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
 
 // Time every candidate launch shape once on this batch and keep the fastest.
 int autotune_plan(Ctx* c, BatchPlan* p, const gsofa_options& o, cudaStream_t st, size_t limit) {
-  std::vector<LaunchShape> cands = candidate_shapes(c, p->n_max, p->label16, limit);
+  std::vector<LaunchShape> cands = candidate_shapes(c, p->n_max, p->label16, limit, o.frontier_order);
   if (cands.empty()) return GSOFA_E_CUDA;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -1148,6 +1235,14 @@ LaunchShape default_shape(Ctx* c, BatchCache& bc, const BatchPlan* p, const gsof
   const uint64_t key = bucket_key(p->n_max, p->N, p->label16) ^ ((uint64_t)o.threads_per_source << 48);
   auto tt = bc.tuned.find(key);
   if (tt != bc.tuned.end() && o.list_capacity == 0 && o.work_chunk == 0) return tt->second;
+  if (o.threads_per_source == 0 && o.list_capacity == 0 && o.work_chunk == 0 && o.frontier_order != 1) {
+    // untuned default: the class-ordered warp tier (fewest expansions)
+    sh.kernel = 1;
+    sh.slots = class_slots(c, p->n_max, 32);
+    if (o.max_ctas > 0 && sh.slots > o.max_ctas * 16) sh.slots = o.max_ctas * 16;
+    if (sh.slots > 0) { *rc = GSOFA_OK; return sh; }
+    sh.kernel = 0;
+  }
   int32_t cap = 0;
   *rc = choose_smem_config(c->sms, limit, p->n_max, p->n_max, p->label16, o.threads_per_source, &sh.block, &sh.occ,
                            &cap);
@@ -1389,7 +1484,42 @@ int gsofa_symbolic_device(int32_t n, const int32_t* d_rowptr, const int32_t* d_c
   int err = GSOFA_OK;
   Ctx* c = get_ctx(&err);
   if (!c) return err;
-  return run_device(c, n, d_rowptr, d_colidx, o, (cudaStream_t)stream, out);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (o.autotune && o.frontier_order == 0 && n > 0) {
+    // time both frontier orders once for this shape and keep the faster
+    int32_t nnz = 0;
+    if (cudaMemcpyAsync(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        wait_stream(st) != GSOFA_OK)
+      return GSOFA_E_CUDA;
+    const std::pair<int32_t, int64_t> key(n, nnz);
+    int best = 0;
+    {
+      std::lock_guard<std::mutex> lk(c->hmu);
+      auto it = c->order_tuned.find(key);
+      if (it != c->order_tuned.end()) best = it->second;
+    }
+    if (best == 0) {
+      float ms[3] = {0.f, 0.f, 0.f};
+      for (int ord = 1; ord <= 2; ord++) {
+        gsofa_options t = o;
+        t.frontier_order = ord;
+        t.collect_stats = 1;
+        t.autotune = 0;
+        for (int rep = 0; rep < 2; rep++) {  // the first run also sizes the row pool
+          gsofa_result r;
+          const int rc = run_device(c, n, d_rowptr, d_colidx, t, st, &r);
+          if (rc) return rc;
+          ms[ord] = r.stats.ms_traverse;
+          gsofa_free(&r);
+        }
+      }
+      best = ms[2] < ms[1] ? 2 : 1;
+      std::lock_guard<std::mutex> lk(c->hmu);
+      c->order_tuned[key] = best;
+    }
+    o.frontier_order = best;
+  }
+  return run_device(c, n, d_rowptr, d_colidx, o, st, out);
 }
 
 int gsofa_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colidx, const gsofa_options* opt,

@@ -5,10 +5,12 @@
 // for large orders) fits under the configured cap.  Each of `streams` stream
 // slots has a dispatcher thread that takes the admitted requests waiting at
 // that moment (up to max_batch) and runs them as one batch (the multi-matrix
-// traversal of gsofa_batch, with pooled workspace); the launches of different
-// slots overlap on the GPU, each limited to its share of the CTAs, so requests
-// that arrive while others are on the device start as soon as a slot and memory
-// free up.  Latency is measured from submission to completion of the result.
+// traversal of gsofa_batch, with pooled workspace).  While one slot's batch is
+// on the GPU the other slot gathers the requests that arrived meanwhile and
+// launches them behind it (its CTAs start as the running batch's CTAs retire,
+// and its size read-back and output assembly overlap the other batch's
+// traversal), so requests start as soon as a slot and memory free up.  Latency
+// is measured from submission to completion of the result.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -195,7 +197,7 @@ int gsofa_server_default_config(gsofa_server_config* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->mem_cap_bytes = (int64_t)150 << 30;
   cfg->max_inflight = 8192;
-  cfg->streams = 3;
+  cfg->streams = 2;
   cfg->max_batch = 512;
   cfg->queue_capacity = 1 << 20;
   gsofa_default_options(&cfg->opts);
@@ -220,11 +222,6 @@ int gsofa_server_create(const gsofa_server_config* cfg, gsofa_server** out) {
   S->sms = device_sms();
   S->smem_max_n = smem_tier_max_order();
   if (S->sms <= 0) { delete S; return GSOFA_E_CUDA; }
-  // each slot's traversal launch gets its share of the CTAs so launches overlap
-  if (S->cfg.opts.max_ctas == 0) {
-    int share = 4 * S->sms / S->cfg.streams;
-    S->cfg.opts.max_ctas = share > 0 ? share : 1;
-  }
   {
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof(props));

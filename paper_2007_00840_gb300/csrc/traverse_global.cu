@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
   const int lane = threadIdx.x & 31;
   const int slot = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (slot >= a.g_slots) return;
-  const int n = a.n;
   const size_t cap = (size_t)a.g_cap, capW = cap / 32, capS = capW / 32;
   Slot sl;
   sl.lab = a.g_lab + (size_t)slot * cap;
@@ -121,13 +120,37 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
   int bad = 0;
 
   for (;;) {
-    int s = -1;
+    int s = -1, mi = 0;
     if (lane == 0) {
       const int k = atomicAdd(&a.ctr->work_global, 1);
-      if (k < a.nsrc && !input_error(a.ctr)) s = a.order ? a.order[k] : a.nsrc - 1 - k;
+      if (k < a.nsrc && !input_error(a.ctr)) {
+        if (a.mats) {  // batch: smallest source index s with item_start[s] <= k
+          int lo = 0, hi = a.n - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.item_start[mid] <= k) hi = mid; else lo = mid + 1;
+          }
+          s = lo;
+          mi = a.mat_order[k - a.item_start[lo]];
+        } else {
+          s = a.order ? a.order[k] : a.nsrc - 1 - k;
+        }
+      }
     }
     s = __shfl_sync(FULL, s, 0);
     if (s < 0) break;
+    mi = __shfl_sync(FULL, mi, 0);
+    int n = a.n;
+    const int32_t* __restrict__ rowptr = a.rowptr;
+    const int32_t* __restrict__ colidx = a.colidx;
+    long long rowb = 0;
+    if (a.mats) {
+      const MatDesc d = a.mats[mi];
+      n = d.n;
+      rowptr = d.rowptr;
+      colidx = d.colidx;
+      rowb = d.row_base;
+    }
 
     // maxId window of this source (values base+1+l for l in [-1, s))
     const uint32_t span = (uint32_t)s + 1u;
@@ -140,10 +163,10 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
     }
 
     // seed: neighbours below s are pending fills with maxId -1; above s, U entries
-    const int rb = __ldg(a.rowptr + s), re = __ldg(a.rowptr + s + 1);
+    const int rb = __ldg(rowptr + s), re = __ldg(rowptr + s + 1);
     int diag = 0;
     for (int e = rb + lane; e < re; e += 32) {
-      const int w = __ldg(a.colidx + e);
+      const int w = __ldg(colidx + e);
       if ((unsigned)w >= (unsigned)n) { bad = 1; continue; }
       if (w < s) {
         sl.lab[w] = base;
@@ -180,13 +203,13 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
       while (qlen > 0) {
         int nq = 0;
         if (single) {  // one vertex: the lanes share its row
-          const int eb = __ldg(a.rowptr + t), ee = __ldg(a.rowptr + t + 1);
+          const int eb = __ldg(rowptr + t), ee = __ldg(rowptr + t + 1);
           if (lane == 0) { n_exp++; n_edge += (unsigned long long)(ee - eb); }
           for (int e0 = eb; e0 < ee; e0 += 32) {
             const int e = e0 + lane;
             int w = 0, enq = 0;
             if (e < ee) {
-              w = __ldg(a.colidx + e);
+              w = __ldg(colidx + e);
               enq = relax_class(sl, w, s, t, pE, n, &bad);
             }
             const unsigned m = __ballot_sync(FULL, enq);
@@ -200,8 +223,8 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
             int eb = 0, ee = 0;
             if (i < qlen) {
               const int v = qc[i];
-              eb = __ldg(a.rowptr + v);
-              ee = __ldg(a.rowptr + v + 1);
+              eb = __ldg(rowptr + v);
+              ee = __ldg(rowptr + v + 1);
               n_exp++;
               n_edge += (unsigned long long)(ee - eb);
             }
@@ -209,7 +232,7 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
             for (int k = 0; k < maxdeg; k++) {
               int w = 0, enq = 0;
               if (eb + k < ee) {
-                w = __ldg(a.colidx + eb + k);
+                w = __ldg(colidx + eb + k);
                 enq = relax_class(sl, w, s, t, pE, n, &bad);
               }
               const unsigned m = __ballot_sync(FULL, enq);
@@ -252,12 +275,16 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
     if (lane == 0) {
       off = atomicAdd(&a.ctr->pool_cursor, (unsigned long long)(nL + nU));
       ok = off + (unsigned long long)(nL + nU) <= (unsigned long long)a.pool_cap;
-      a.row_off[s] = ok ? (int64_t)off : -1;
-      a.row_nL[s] = nL;
-      a.row_nU[s] = nU;
-      a.fill_count[s] = nL + nU - ((re - rb) + (diag ? 0 : 1));
+      a.row_off[rowb + s] = ok ? (int64_t)off : -1;
+      a.row_nL[rowb + s] = nL;
+      a.row_nU[rowb + s] = nU;
+      a.fill_count[rowb + s] = nL + nU - ((re - rb) + (diag ? 0 : 1));
       atomicAdd(&a.ctr->total_L, (unsigned long long)nL);
       atomicAdd(&a.ctr->total_U, (unsigned long long)nU);
+      if (a.mat_tot) {
+        atomicAdd(&a.mat_tot[2 * mi], (unsigned long long)nL);
+        atomicAdd(&a.mat_tot[2 * mi + 1], (unsigned long long)nU);
+      }
       if (ok) a.pool[off + nL] = (uint32_t)s;
       else atomicOr(&a.ctr->err, ERR_OVERFLOW);
     }

@@ -74,6 +74,16 @@ def test_adversarial_shapes():
             assert_same(h, oracle_full(A)), (A.name, opt)
 
 
+def test_frontier_orders_and_autotune():
+    """Breadth-first, class-ordered and autotuned frontier orders give the same rows."""
+    cases = [synth.grid2d(40, 0.7, seed=21), synth.banded(2500, 30, seed=22),
+             synth.grid2d_nd(60, 0.8, seed=23, leaf=16), synth.random_pattern(300, 0.02, seed=24, diag=False)]
+    for A in cases:
+        o = oracle_full(A)
+        for opt in ({"frontier_order": 1}, {"frontier_order": 2}, {"autotune": 1}, {"autotune": 1}):
+            assert_same(run_gpu(A, **opt), o), (A.name, opt)
+
+
 def test_empty_matrix():
     A = synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), "empty")
     h = run_gpu(A)
