@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="served: stream length")
-    ap.add_argument("--rate-frac", type=float, default=0.7, help="served: arrival rate / batched req/s")
+    ap.add_argument("--rate-frac", type=float, default=0.7, help="served: arrival rate / saturated req/s")
+    ap.add_argument("--opt", action="append", default=[], help="library option NAME=VALUE (repeatable)")
     return ap.parse_args()
 
 
@@ -193,7 +194,8 @@ def main():
     rp = torch.from_numpy(A.rowptr).to(dev)
     ci = torch.from_numpy(A.colidx).to(dev)
     stream = torch.cuda.current_stream(dev)
-    opts = gs.options(collect_stats=1)
+    extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
+    opts = gs.options(collect_stats=1, **extra)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
 
     def barrier():
@@ -298,7 +300,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded)",
-        "config": {"workload": name, "n": n, "nnz_A": A.nnz, "nnz_LU": int(nnz_step),
+        "config": {"workload": name, "n": n, "nnz_A": A.nnz, "nnz_LU": int(nnz_step), "options": extra,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "rows_per_s": rows_per_s,
         "wall_s": wall,

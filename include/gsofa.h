@@ -72,7 +72,12 @@ typedef struct gsofa_options {
     int32_t frontier_order;      /* 0: automatic; 1: breadth-first levels (shared-memory tier wherever the
                                     maxId array fits on chip); 2: by increasing maxId class (warp tier).
                                     Same result; with autotune = 1 the faster one is kept per shape */
-    int32_t reserved[2];
+    int32_t label_bits;          /* shared-memory tier maxId width: 0 automatic (16 when n <= 65533), 16 or 32 */
+    int32_t expand_mode;         /* shared-memory tier row access: 0 automatic, 1 CSR row slots per lane,
+                                    2 CSR edge-balanced (a warp flattens its rows' entries), 3 16-byte
+                                    records of 16-bit column offsets built from the CSR (rows that do
+                                    not fit fall back to the CSR) */
+    int32_t reserved[3];
 } gsofa_options;
 
 /* Per-call statistics (filled when options.collect_stats == 1). */
@@ -84,6 +89,9 @@ typedef struct gsofa_stats {
     int64_t vertices_expanded;   /* frontier expansions, revisits included */
     int64_t edges_scanned;       /* adjacency entries read by expansions */
     int64_t pool_retries;        /* times the row pool had to grow and the traversal rerun */
+    int64_t levels;              /* shared-memory tier: frontier levels summed over sources */
+    int64_t cycles_traverse;     /* shared-memory tier: SM cycles in frontier levels, summed over sources */
+    int64_t cycles_emit;         /* shared-memory tier: SM cycles emitting rows, summed over sources */
 } gsofa_stats;
 
 /* Result.  Arrays are owned by the library and released by gsofa_free().

@@ -35,7 +35,9 @@ class gsofa_options(ctypes.Structure):
         ("list_capacity", ctypes.c_int32),
         ("max_ctas", ctypes.c_int32),
         ("frontier_order", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("label_bits", ctypes.c_int32),
+        ("expand_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -53,6 +55,9 @@ class gsofa_stats(ctypes.Structure):
         ("vertices_expanded", ctypes.c_int64),
         ("edges_scanned", ctypes.c_int64),
         ("pool_retries", ctypes.c_int64),
+        ("levels", ctypes.c_int64),
+        ("cycles_traverse", ctypes.c_int64),
+        ("cycles_emit", ctypes.c_int64),
     ]
 
 

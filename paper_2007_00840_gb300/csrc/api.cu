@@ -311,7 +311,7 @@ namespace {
 
 int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   const int stat = trav_smem_static_bytes();
-  const int label16 = n <= 65533 ? 1 : 0;
+  const int label16 = (n <= 65533 && o.label_bits != 32) ? 1 : 0;
   const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
   int32_t S = trav_smem_max_S(n, limit, label16);
   if (o.smem_max_source > 0 && o.smem_max_source < S) S = o.smem_max_source;
@@ -325,7 +325,9 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     int32_t cap = 0;
     const int rc = choose_smem_config(c->sms, limit, n, S, label16, o.threads_per_source, &block, &occ, &cap);
     if (rc) return rc;
-    if (o.list_capacity > 0 && o.list_capacity < cap) cap = o.list_capacity < 32 ? 32 : o.list_capacity;
+    // a short shared list leaves more L1 for the rows; the rest spills to global memory
+    const int32_t want = o.list_capacity > 0 ? o.list_capacity : 2048;
+    if (want < cap) cap = want < 32 ? 32 : want;
     if (cap > S) cap = S;
     p->list_cap = cap;
     p->smem_block = block;
@@ -366,6 +368,10 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   if (in->max_ctas < 0 || in->frontier_order < 0 || in->frontier_order > 2) return GSOFA_E_INVAL;
   o->max_ctas = in->max_ctas;
   o->frontier_order = in->frontier_order;
+  if (in->label_bits != 0 && in->label_bits != 16 && in->label_bits != 32) return GSOFA_E_INVAL;
+  o->label_bits = in->label_bits;
+  if (in->expand_mode < 0 || in->expand_mode > 3) return GSOFA_E_INVAL;
+  o->expand_mode = in->expand_mode;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -404,6 +410,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   int64_t* flag_pos = nullptr;
   int32_t* spill = nullptr;
   int64_t spill_cap = 0;
+  int4* ell = nullptr;
   DevCounters* h = pinned_counters();
   Plan plan;
   long long pool_cap = 0;
@@ -448,6 +455,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   if (plan.S > 0) {
     spill_cap = plan.S > plan.list_cap ? plan.S - plan.list_cap : 1;
     CK(palloc(c, &spill, (size_t)plan.smem_grid * 2 * (size_t)spill_cap, st));
+    if (o.expand_mode == 0 || o.expand_mode == 3) CK(palloc(c, &ell, (size_t)n, st));
   }
   // order: shared tier [S-1 .. 0] then global tier [n-1 .. S] (largest source first)
   LK(launch_iota_desc(order, plan.S, plan.S, st));
@@ -469,6 +477,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     } else {
       ev.rec(1, st);
     }
+    if (ell && attempt == 0) LK(launch_build_ell(n, d_rowptr, d_colidx, ell, ctr, st));
     TravArgs a;
     std::memset(&a, 0, sizeof(a));
     a.n = n;
@@ -512,6 +521,8 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.spill = spill;
       a.spill_cap = spill_cap;
       a.chunk = o.work_chunk > 0 ? o.work_chunk : 1;
+      a.expand_mode = o.expand_mode == 0 ? 3 : o.expand_mode;
+      a.ell = ell;
       LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, plan.label16, st));
     }
     ev.rec(4, st);
@@ -545,6 +556,9 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   out->n_super = h->n_super;
   out->stats.vertices_expanded = (int64_t)h->expansions;
   out->stats.edges_scanned = (int64_t)h->edges;
+  out->stats.levels = (int64_t)h->levels;
+  out->stats.cycles_traverse = (int64_t)h->cyc_trav;
+  out->stats.cycles_emit = (int64_t)h->cyc_emit;
   out->stats.traverse_launches = (plan.S > 0) + (plan.S < n);
 
   CK(palloc(c, &out->L_rowptr, (size_t)n + 1, st));
@@ -576,6 +590,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   pfree(flags, st);
   pfree(flag_pos, st);
   pfree(spill, st);
+  pfree(ell, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   scan_tmp = nullptr;
 
@@ -606,6 +621,7 @@ fail:
   pfree(flags, st);
   pfree(flag_pos, st);
   pfree(spill, st);
+  pfree(ell, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   {
     const int32_t det = out->err_detail;
@@ -827,6 +843,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.nmats = p.B;
   a.chunk = p.shape.work_chunk;
   a.mat_tot = p.mat_tot();
+  a.expand_mode = (o.expand_mode == 0 || o.expand_mode == 3) ? 1 : o.expand_mode;
   // while capturing, external records become event nodes of the graph
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);

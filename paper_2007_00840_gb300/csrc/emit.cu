@@ -54,6 +54,9 @@ __global__ void init_counters_kernel(DevCounters* c) {
     c->n_super = 0;
     c->work_smem = 0;
     c->work_global = 0;
+    c->levels = 0ull;
+    c->cyc_trav = 0ull;
+    c->cyc_emit = 0ull;
   }
 }
 
@@ -531,4 +534,48 @@ cudaError_t launch_compact_long(int64_t nrows, const uint32_t* pool, const int64
   return launch_compact((int32_t)nrows, pool, row_off, row_nL, row_nU, L_off, U_off, L_colidx, U_colidx, st);
 }
 
+}  // namespace gsofa
+
+// ------------------------------------------------------------- ELL copy
+// Row v of A without its diagonal as up to 8 signed 16-bit offsets w - v in one
+// 16-byte record, padded with 0 (an offset of 0 names v itself, which the
+// traversal skips).  Rows with more entries or offsets beyond +-32767 get the
+// marker -32768 in slot 0 and are read from the CSR instead.
+namespace gsofa {
+__global__ void build_ell_kernel(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                 int4* __restrict__ ell, DevCounters* ctr) {
+  if (input_error(ctr)) return;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int rb = rowptr[v], re = rowptr[v + 1];
+    short off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int k = 0;
+    bool fits = true;
+    for (int e = rb; e < re; e++) {
+      const long long d = (long long)colidx[e] - v;
+      if (d == 0) continue;
+      if (k == 8 || d > 32767 || d < -32767) { fits = false; break; }
+      off[k++] = (short)d;
+    }
+    if (!fits) {
+      off[0] = (short)-32768;
+      for (int q = 1; q < 8; q++) off[q] = 0;
+    }
+    int4 r;
+    r.x = (int)(((unsigned)(unsigned short)off[1] << 16) | (unsigned short)off[0]);
+    r.y = (int)(((unsigned)(unsigned short)off[3] << 16) | (unsigned short)off[2]);
+    r.z = (int)(((unsigned)(unsigned short)off[5] << 16) | (unsigned short)off[4]);
+    r.w = (int)(((unsigned)(unsigned short)off[7] << 16) | (unsigned short)off[6]);
+    ell[v] = r;
+  }
+}
+
+cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ell, DevCounters* ctr,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = ((long long)n + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  build_ell_kernel<<<(int)grid, block, 0, st>>>(n, rowptr, colidx, ell, ctr);
+  return cudaGetLastError();
+}
 }  // namespace gsofa

@@ -34,6 +34,9 @@ struct DevCounters {
   int32_t work_smem;                // work counter of the shared-memory tier
   int32_t work_global;              // work counter of the global tier
   int32_t pad[3];
+  unsigned long long levels;        // frontier levels over all sources (stats)
+  unsigned long long cyc_trav;      // SM cycles in frontier levels (stats, thread 0 of each CTA)
+  unsigned long long cyc_emit;      // SM cycles in row emission (stats)
 };
 
 // Input errors found so far (read through L2, not a cached copy).
@@ -73,6 +76,8 @@ struct TravArgs {
   int32_t fill_first;                 // optional "line 9.5" of Section 4
   int32_t collect_stats;
   int32_t counts_only;                // 1: write per-row counts only (no pool, no row_off)
+  int32_t expand_mode;                // shared tier: 1 row slots, 2 edge-balanced
+  const int4* ell;                    // shared tier: 16-bit offset copy of A (null: CSR only)
   // batch mode (mats != nullptr): item k -> source s (descending) and matrix m;
   // item_start[s] = number of items with a larger source index, mat_order lists
   // matrices by decreasing order n; n above is the largest order in the batch
@@ -138,6 +143,8 @@ cudaError_t launch_scatter_starts(int32_t n, const int32_t* flags, const int64_t
                                   int32_t* super_start, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t st);
 cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
+cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ell, DevCounters* ctr,
+                             cudaStream_t st);
 cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
 
 // host helpers (api.cu)

@@ -108,6 +108,7 @@ extern "C" int gsofa_row_counts_noalloc(int32_t n, const int32_t* d_rowptr, cons
     a.fill_count = d_fill_count;
     a.ctr = ctr;
     a.counts_only = 1;
+    a.expand_mode = 1;
     if (launch_trav_smem(a, (int)grid, block, label16, st) != cudaSuccess) return GSOFA_E_CUDA;
   }
   DevCounters h;

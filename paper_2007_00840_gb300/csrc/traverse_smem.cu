@@ -38,7 +38,8 @@ namespace gsofa {
 namespace {
 
 constexpr int BIG_DEG = 32;
-constexpr int BATCH = 8;  // column loads issued together per frontier vertex
+constexpr int BATCH = 8;      // column loads issued together per frontier vertex (row slots)
+constexpr int EB_UNROLL = 4;  // flattened chunks of 32 entries loaded together (edge-balanced)
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
@@ -136,7 +137,11 @@ size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
   return label16 ? trav_smem_bytes_t<uint16_t>(n, S, cap) : trav_smem_bytes_t<uint32_t>(n, S, cap);
 }
 
-template <typename LabT>
+// EB: edge-balanced expansion (the warp flattens the rows of its 32 frontier
+// vertices so every lane works on an entry) instead of lock-step row slots.
+// FF: the optional fill-first check of Section 4.
+// ELL: read rows from the 16-bit offset records (CSR only for rows that do not fit).
+template <typename LabT, bool EB, bool FF, bool ELL>
 __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n_max = a.n, S = a.S, CAP = a.list_cap;
@@ -259,13 +264,16 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     // vertices below s have at most s hops, so level s+2 changes nothing.
     const int cap_lv = s + 3;
     int qc = s_q[0];
-    for (int L = 1; qc > 0; L++) {
+    long long t_start = 0;
+    if (a.collect_stats && tid == 0) t_start = clock64();
+    int L = 1;
+    for (; qc > 0; L++) {
       const int cb = (L - 1) & 1, nb = L & 1;
       LabT* Lc = cb ? L1 : L0;
       int32_t* Sc = cb ? S1 : S0;
       uint32_t* Dc = cb ? D1 : D0;
       Src<LabT> c{lab, ub, nb ? D1 : D0, nb ? L1 : L0, nb ? S1 : S0, &s_q[L % 3], base, s, n, CAP,
-                  a.fill_first};
+                  FF ? 1 : 0};
       if (tid == 0) s_q[(L + 1) % 3] = 0;
       for (int r0 = warp * 32; r0 < qc; r0 += nthr) {
         const int r = r0 + lane;
@@ -273,25 +281,142 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         uint32_t nmE = 0u;
         if (r < qc) {
           v = r < CAP ? (int)Lc[r] : Sc[r - CAP];
-          atomicAnd(&Dc[v >> 5], ~(1u << (v & 31)));  // v leaves the current list
-          eb = __ldg(rowptr + v);
-          ee = __ldg(rowptr + v + 1);
+          // v leaves the current list.  Nothing sets bits of Dc during this level
+          // and every vertex with a bit in Dc is dequeued in it, so the word can
+          // simply be zeroed.
+          Dc[v >> 5] = 0u;
+          if (!ELL || a.collect_stats) {
+            eb = __ldg(rowptr + v);
+            ee = __ldg(rowptr + v + 1);
+          }
           const uint32_t lv = (uint32_t)lab[v];
           const uint32_t vE = base + 1u + (uint32_t)v;
           nmE = lv > vE ? lv : vE;  // encoded max(maxId(v), v)
           n_exp++;
           n_edge += (unsigned long long)(ee - eb);
         }
+        if (EB && !ELL) {
+          // flattened entries of the warp's rows; entry e belongs to the lane
+          // whose inclusive degree sum first exceeds e
+          const int deg = v >= 0 ? ee - eb : 0;
+          const int incl = warp_incl_scan(deg, lane);
+          const int total = __shfl_sync(FULL, incl, 31);
+          for (int c0 = 0; c0 < total; c0 += 32 * EB_UNROLL) {
+            int wv[EB_UNROLL], ov[EB_UNROLL];
+            uint32_t onm[EB_UNROLL];
+#pragma unroll
+            for (int u = 0; u < EB_UNROLL; u++) {
+              const int e = c0 + 32 * u + lane;
+              int o = 0;
+#pragma unroll
+              for (int b = 16; b >= 1; b >>= 1) {
+                const int t = __shfl_sync(FULL, incl, o + b - 1);
+                if (t <= e) o += b;
+              }
+              const int oc = o < 31 ? o : 31;
+              const int o_excl = __shfl_sync(FULL, incl - deg, oc);
+              const int o_eb = __shfl_sync(FULL, eb, oc);
+              ov[u] = __shfl_sync(FULL, v, oc);
+              onm[u] = __shfl_sync(FULL, nmE, oc);
+              wv[u] = e < total ? __ldg(colidx + o_eb + (e - o_excl)) : ov[u];
+            }
+            unsigned em = 0u;
+#pragma unroll
+            for (int u = 0; u < EB_UNROLL; u++)
+              if (wv[u] != ov[u] && relax(c, wv[u], onm[u], &bad)) em |= 1u << u;  // diagonal skipped
+            const int cnt = __popc(em);
+            const int inc2 = warp_incl_scan(cnt, lane);
+            const int tot = __shfl_sync(FULL, inc2, 31);
+            if (tot) {
+              int basep = 0;
+              if (lane == 31) basep = atomicAdd(c.qn, tot);
+              basep = __shfl_sync(FULL, basep, 31);
+              int pos = basep + inc2 - cnt;
+#pragma unroll
+              for (int u = 0; u < EB_UNROLL; u++) {
+                if ((em >> u) & 1u) {
+                  if (pos < CAP) c.Ln[pos] = (LabT)wv[u]; else c.Sn[pos - CAP] = wv[u];
+                  pos++;
+                }
+              }
+            }
+          }
+          continue;
+        }
+        if (ELL) {
+          // one 16-byte record per row: up to 8 offsets w - v (0 = skip)
+          bool fb = false;
+          int wv[8];
+          if (v >= 0) {
+            const int4 r4 = __ldg(a.ell + v);
+            const uint32_t h[4] = {(uint32_t)r4.x, (uint32_t)r4.y, (uint32_t)r4.z, (uint32_t)r4.w};
+            fb = (h[0] & 0xFFFFu) == 0x8000u;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              wv[2 * q] = v + (int)(short)(h[q] & 0xFFFFu);
+              wv[2 * q + 1] = v + (int)(short)(h[q] >> 16);
+            }
+            if (fb) {
+#pragma unroll
+              for (int q = 0; q < 8; q++) wv[q] = v;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) wv[q] = v;
+          }
+          unsigned em = 0u;
+#pragma unroll
+          for (int q = 0; q < 8; q++)
+            if (wv[q] != v && relax(c, wv[q], nmE, &bad)) em |= 1u << q;
+          const int cnt = __popc(em);
+          const int incl = warp_incl_scan(cnt, lane);
+          const int tot = __shfl_sync(FULL, incl, 31);
+          if (tot) {
+            int basep = 0;
+            if (lane == 31) basep = atomicAdd(c.qn, tot);
+            basep = __shfl_sync(FULL, basep, 31);
+            int pos = basep + incl - cnt;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+              if ((em >> q) & 1u) {
+                if (pos < CAP) c.Ln[pos] = (LabT)wv[q]; else c.Sn[pos - CAP] = wv[q];
+                pos++;
+              }
+            }
+          }
+          if (!__any_sync(FULL, fb)) continue;
+          if (!fb) v = -1;  // rows that did not fit the record continue below from the CSR
+          if (v >= 0) {
+            eb = __ldg(rowptr + v);
+            ee = __ldg(rowptr + v + 1);
+          }
+        }
         const int deg = (v >= 0 && ee - eb <= BIG_DEG) ? ee - eb : 0;
         const int maxdeg = __reduce_max_sync(FULL, deg);
         for (int k0 = 0; k0 < maxdeg; k0 += BATCH) {
           int wv[BATCH];  // independent loads first, then the relaxations
 #pragma unroll
-          for (int q = 0; q < BATCH; q++) wv[q] = (k0 + q < deg) ? __ldg(colidx + eb + k0 + q) : 0;
+          for (int q = 0; q < BATCH; q++) wv[q] = (k0 + q < deg) ? __ldg(colidx + eb + k0 + q) : v;
+          unsigned em = 0u;  // slots whose vertex joins the next frontier
 #pragma unroll
-          for (int q = 0; q < BATCH; q++) {
-            const int enq = (k0 + q < deg) ? relax(c, wv[q], nmE, &bad) : 0;
-            append(c, enq, wv[q], lane);
+          for (int q = 0; q < BATCH; q++)
+            if (wv[q] != v && relax(c, wv[q], nmE, &bad)) em |= 1u << q;  // the diagonal entry is skipped
+          // one shared atomic per warp for the whole batch
+          const int cnt = __popc(em);
+          const int incl = warp_incl_scan(cnt, lane);
+          const int tot = __shfl_sync(FULL, incl, 31);
+          if (tot) {
+            int basep = 0;
+            if (lane == 31) basep = atomicAdd(c.qn, tot);
+            basep = __shfl_sync(FULL, basep, 31);
+            int pos = basep + incl - cnt;
+#pragma unroll
+            for (int q = 0; q < BATCH; q++) {
+              if ((em >> q) & 1u) {
+                if (pos < CAP) c.Ln[pos] = (LabT)wv[q]; else c.Sn[pos - CAP] = wv[q];
+                pos++;
+              }
+            }
           }
         }
         unsigned bigm = __ballot_sync(FULL, v >= 0 && (ee - eb) > BIG_DEG);
@@ -300,10 +425,11 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           bigm &= bigm - 1;
           const int beb = __shfl_sync(FULL, eb, l), bee = __shfl_sync(FULL, ee, l);
           const uint32_t bnm = __shfl_sync(FULL, nmE, l);
+          const int bv = __shfl_sync(FULL, v, l);
           for (int e0 = beb; e0 < bee; e0 += 32) {
             const int e = e0 + lane;
-            const int w = e < bee ? __ldg(colidx + e) : 0;
-            const int enq = e < bee ? relax(c, w, bnm, &bad) : 0;
+            const int w = e < bee ? __ldg(colidx + e) : bv;
+            const int enq = w != bv ? relax(c, w, bnm, &bad) : 0;
             append(c, enq, w, lane);
           }
         }
@@ -325,6 +451,12 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       }
     }
 
+    long long t_mid = 0;
+    if (a.collect_stats && tid == 0) {
+      t_mid = clock64();
+      atomicAdd(&a.ctr->levels, (unsigned long long)(L - 1));
+      atomicAdd(&a.ctr->cyc_trav, (unsigned long long)(t_mid - t_start));
+    }
     // ---- emission: counts, pool offset, sorted row
     const int perL = (((s + nwarps - 1) / nwarps) + 31) & ~31;
     const int loL = warp * perL, hiL = min(s, loL + perL);
@@ -404,6 +536,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         pos += __shfl_sync(FULL, inc, 31);
       }
     }
+    if (a.collect_stats && tid == 0) atomicAdd(&a.ctr->cyc_emit, (unsigned long long)(clock64() - t_mid));
   }
 
   if (bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
@@ -435,25 +568,34 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16) {
   return label16 ? max_S_t<uint16_t>(n, smem_limit, 1024) : max_S_t<uint32_t>(n, smem_limit, 1024);
 }
 
+template <typename LabT, bool EB, bool FF, bool ELL>
+static cudaError_t launch_t(const TravArgs& a, int grid, int block, size_t bytes, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<LabT, EB, FF, ELL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  trav_smem_kernel<LabT, EB, FF, ELL><<<grid, block, bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename LabT>
+static cudaError_t launch_l(const TravArgs& a, int grid, int block, size_t bytes, cudaStream_t st) {
+  const bool ff = a.fill_first != 0;
+  if (a.ell) return ff ? launch_t<LabT, false, true, true>(a, grid, block, bytes, st)
+                       : launch_t<LabT, false, false, true>(a, grid, block, bytes, st);
+  if (a.expand_mode == 2) return ff ? launch_t<LabT, true, true, false>(a, grid, block, bytes, st)
+                                    : launch_t<LabT, true, false, false>(a, grid, block, bytes, st);
+  return ff ? launch_t<LabT, false, true, false>(a, grid, block, bytes, st)
+            : launch_t<LabT, false, false, false>(a, grid, block, bytes, st);
+}
+
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st) {
   const size_t bytes = trav_smem_bytes(a.n, a.S, a.list_cap, label16);
-  if (label16) {
-    cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return e;
-    trav_smem_kernel<uint16_t><<<grid, block, bytes, st>>>(a);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return e;
-    trav_smem_kernel<uint32_t><<<grid, block, bytes, st>>>(a);
-  }
-  return cudaGetLastError();
+  return label16 ? launch_l<uint16_t>(a, grid, block, bytes, st) : launch_l<uint32_t>(a, grid, block, bytes, st);
 }
 
 int trav_smem_static_bytes() {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t>) != cudaSuccess) {
+  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t, false, false, false>) != cudaSuccess) {
     cudaGetLastError();
     return 1024;
   }
@@ -461,7 +603,8 @@ int trav_smem_static_bytes() {
 }
 
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16) {
-  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t> : (const void*)trav_smem_kernel<uint32_t>;
+  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t, false, false, true>
+                          : (const void*)trav_smem_kernel<uint32_t, false, false, true>;
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;

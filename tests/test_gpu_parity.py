@@ -69,7 +69,8 @@ def test_adversarial_shapes():
     cases.append(synth._csr_from_pairs(2, np.array([0, 1]), np.array([1, 0]), "n2_swap"))
     cases.append(synth.random_pattern(70, 1.0, seed=1))
     for A in cases:
-        for opt in ({}, {"smem_max_source": -1}, {"fill_first": 1}):
+        for opt in ({}, {"smem_max_source": -1}, {"fill_first": 1}, {"expand_mode": 2},
+                    {"expand_mode": 2, "fill_first": 1, "list_capacity": 32}):
             h = run_gpu(A, **opt)
             assert_same(h, oracle_full(A)), (A.name, opt)
 
@@ -80,7 +81,9 @@ def test_frontier_orders_and_autotune():
              synth.grid2d_nd(60, 0.8, seed=23, leaf=16), synth.random_pattern(300, 0.02, seed=24, diag=False)]
     for A in cases:
         o = oracle_full(A)
-        for opt in ({"frontier_order": 1}, {"frontier_order": 2}, {"autotune": 1}, {"autotune": 1}):
+        for opt in ({"frontier_order": 1}, {"frontier_order": 2}, {"autotune": 1}, {"autotune": 1},
+                    {"expand_mode": 2}, {"expand_mode": 2, "label_bits": 32}, {"label_bits": 32, "fill_first": 1},
+                    {"expand_mode": 1}, {"expand_mode": 3, "label_bits": 32}):
             assert_same(run_gpu(A, **opt), o), (A.name, opt)
 
 
@@ -123,6 +126,8 @@ def test_workload_grid3d_32():
     h = run_gpu(A)
     assert_same(h, o)
     assert h.nnz_L + h.nnz_U == int(o["L_rowptr"][-1] + o["U_rowptr"][-1])
+    assert_same(run_gpu(A, expand_mode=2), o)
+    assert_same(run_gpu(A, expand_mode=1), o)
 
 
 def test_workload_nd_1m_sampled():
