@@ -551,9 +551,12 @@ __global__ void build_ell_kernel(int32_t n, const int32_t* __restrict__ rowptr, 
     int k = 0;
     bool fits = true;
     for (int e = rb; e < re; e++) {
-      const long long d = (long long)colidx[e] - v;
+      const int w = colidx[e];
+      const long long d = (long long)w - v;
       if (d == 0) continue;
-      if (k == 8 || d > 32767 || d < -32767) { fits = false; break; }
+      // out-of-range columns (possible only when validation is skipped) go to the
+      // CSR path, which checks them
+      if (k == 8 || d > 32767 || d < -32767 || w < 0 || w >= n) { fits = false; break; }
       off[k++] = (short)d;
     }
     if (!fits) {

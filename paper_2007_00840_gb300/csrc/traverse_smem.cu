@@ -41,6 +41,7 @@ constexpr int BIG_DEG = 32;
 constexpr int BATCH = 8;      // column loads issued together per frontier vertex (row slots)
 constexpr int EB_UNROLL = 4;  // flattened chunks of 32 entries loaded together (edge-balanced)
 
+
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -56,21 +57,31 @@ struct LabOps;
 template <>
 struct LabOps<uint32_t> {
   static constexpr uint32_t MAXV = 0xFFFFFFFFu;
-  static __device__ __forceinline__ uint32_t amin(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+  // lab[w] = min(lab[w], v); *old = the previous value; true iff it decreased
+  static __device__ __forceinline__ bool lower(uint32_t* lab, int w, uint32_t v, uint32_t* old) {
+    *old = atomicMin(lab + w, v);
+    return v < *old;
+  }
 };
 
 template <>
 struct LabOps<uint16_t> {
   static constexpr uint32_t MAXV = 0xFFFFu;
-  // 16-bit atomic minimum by compare-and-swap; returns the previous value
-  static __device__ __forceinline__ uint32_t amin(uint16_t* p, uint32_t v) {
-    unsigned short old = *(volatile unsigned short*)p;
-    while (v < old) {
-      const unsigned short prev = atomicCAS((unsigned short*)p, old, (unsigned short)v);
-      if (prev == old) break;
-      old = prev;
+  // lab[w] = min(lab[w], v) by compare-and-swap on the aligned 32-bit word that
+  // holds lab[w] and its neighbour; *old = the previous value; true iff it decreased
+  static __device__ __forceinline__ bool lower(uint16_t* lab, int w, uint32_t v, uint32_t* old) {
+    uint32_t* wp = reinterpret_cast<uint32_t*>(lab) + (w >> 1);
+    const int sh = (w & 1) << 4;
+    uint32_t word = *(volatile uint32_t*)wp;
+    uint32_t cur = (word >> sh) & 0xFFFFu;
+    while (v < cur) {
+      const uint32_t prev = atomicCAS(wp, word, (word & ~(0xFFFFu << sh)) | (v << sh));
+      if (prev == word) { *old = cur; return true; }
+      word = prev;
+      cur = (word >> sh) & 0xFFFFu;
     }
-    return old;
+    *old = cur;
+    return false;
   }
 };
 
@@ -83,24 +94,55 @@ struct Src {
   int32_t* Sn;       // list being built (spilled part)
   int* qn;           // its length counter
   uint32_t base;
-  int32_t s, n, cap, fill_first;
+  int32_t s, n, cap;
 };
+
+// relax() for a neighbour w < s (no range check: callers guarantee w in [0, s)).
+template <typename LabT, bool FF>
+__device__ __forceinline__ int relax_low(const Src<LabT>& c, int w, uint32_t nmE) {
+  const uint32_t wE = c.base + 1u + (uint32_t)w;
+  if (FF && (uint32_t)c.lab[w] < wE) return 0;
+  uint32_t old;
+  if (!LabOps<LabT>::lower(c.lab, w, nmE, &old) || old <= wE) return 0;
+  const uint32_t bit = 1u << (w & 31);
+  if (c.Dn[w >> 5] & bit) return 0;
+  return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
+}
+
+// relax() when every vertex of the matrix has a label slot ("U by labels"):
+// a neighbour w > s is recorded as a U entry by lowering its label into the
+// current window, like any other vertex, so there is no U branch; only w < s
+// can join the frontier.  w in [0, n) is the caller's guarantee; w == s and
+// w == f are harmless (s is never read back, f's own proposal never lowers it).
+template <typename LabT, bool FF>
+__device__ __forceinline__ int relax_ul(const Src<LabT>& c, int w, uint32_t nmE) {
+  const uint32_t wE = c.base + 1u + (uint32_t)w;
+  if (FF && w < c.s && (uint32_t)c.lab[w] < wE) return 0;
+  uint32_t old;
+  if (!LabOps<LabT>::lower(c.lab, w, nmE, &old) || w >= c.s || old <= wE) return 0;
+  const uint32_t bit = 1u << (w & 31);
+  if (c.Dn[w >> 5] & bit) return 0;
+  return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
+}
+
+// relax() for a neighbour read from an ELL record: w is in [0, n) and w != f
+// by construction of the records, so neither is checked here.
+template <typename LabT, bool FF, bool UL>
+__device__ __forceinline__ int relax_rec(const Src<LabT>& c, int w, uint32_t nmE) {
+  if (UL) return relax_ul<LabT, FF>(c, w, nmE);
+  if (w < c.s) return relax_low<LabT, FF>(c, w, nmE);
+  if (w > c.s) atomicOr(&c.ub[w >> 5], 1u << (w & 31));
+  return 0;
+}
 
 // Decide edge (f -> w) with encoded proposal nmE.  Returns 1 if w must be
 // appended to the next frontier (its dedup bit was set here).
-template <typename LabT>
+template <typename LabT, bool FF, bool UL>
 __device__ __forceinline__ int relax(const Src<LabT>& c, int w, uint32_t nmE, int* bad) {
   if ((unsigned)w >= (unsigned)c.n) { *bad = 1; return 0; }
-  if (w < c.s) {
-    const uint32_t wE = c.base + 1u + (uint32_t)w;   // encoded value of maxId == w
-    if (c.fill_first && (uint32_t)c.lab[w] < wE) return 0;  // already a fill: proposal stays w
-    const uint32_t old = LabOps<LabT>::amin(&c.lab[w], nmE);
-    if (nmE < old && old > wE) {
-      const uint32_t bit = 1u << (w & 31);
-      if (c.Dn[w >> 5] & bit) return 0;
-      return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
-    }
-  } else if (w > c.s) {
+  if (UL) return relax_ul<LabT, FF>(c, w, nmE);
+  if (w < c.s) return relax_low<LabT, FF>(c, w, nmE);
+  if (w > c.s) {
     const uint32_t bit = 1u << (w & 31);
     if (!(c.ub[w >> 5] & bit)) atomicOr(&c.ub[w >> 5], bit);
   }
@@ -141,7 +183,7 @@ size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
 // vertices so every lane works on an entry) instead of lock-step row slots.
 // FF: the optional fill-first check of Section 4.
 // ELL: read rows from the 16-bit offset records (CSR only for rows that do not fit).
-template <typename LabT, bool EB, bool FF, bool ELL>
+template <typename LabT, bool EB, bool FF, bool ELL, bool UL>
 __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n_max = a.n, S = a.S, CAP = a.list_cap;
@@ -252,7 +294,8 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           if (pos < CAP) L0[pos] = (LabT)w; else S0[pos - CAP] = w;
         }
       } else if (w > s) {
-        atomicOr(&ub[w >> 5], 1u << (w & 31));
+        if (UL) lab[w] = (LabT)base;  // any value of the window marks a U entry
+        else atomicOr(&ub[w >> 5], 1u << (w & 31));
       } else {
         s_diag = 1;
       }
@@ -272,8 +315,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       LabT* Lc = cb ? L1 : L0;
       int32_t* Sc = cb ? S1 : S0;
       uint32_t* Dc = cb ? D1 : D0;
-      Src<LabT> c{lab, ub, nb ? D1 : D0, nb ? L1 : L0, nb ? S1 : S0, &s_q[L % 3], base, s, n, CAP,
-                  FF ? 1 : 0};
+      Src<LabT> c{lab, ub, nb ? D1 : D0, nb ? L1 : L0, nb ? S1 : S0, &s_q[L % 3], base, s, n, CAP};
       if (tid == 0) s_q[(L + 1) % 3] = 0;
       for (int r0 = warp * 32; r0 < qc; r0 += nthr) {
         const int r = r0 + lane;
@@ -323,7 +365,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
             unsigned em = 0u;
 #pragma unroll
             for (int u = 0; u < EB_UNROLL; u++)
-              if (wv[u] != ov[u] && relax(c, wv[u], onm[u], &bad)) em |= 1u << u;  // diagonal skipped
+              if (wv[u] != ov[u] && relax<LabT, FF, UL>(c, wv[u], onm[u], &bad)) em |= 1u << u;  // diagonal skipped
             const int cnt = __popc(em);
             const int inc2 = warp_incl_scan(cnt, lane);
             const int tot = __shfl_sync(FULL, inc2, 31);
@@ -344,7 +386,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           continue;
         }
         if (ELL) {
-          // one 16-byte record per row: up to 8 offsets w - v (0 = skip)
+          // one 16-byte record per row: up to 8 offsets w - v (0 = empty)
           bool fb = false;
           int wv[8];
           if (v >= 0) {
@@ -367,7 +409,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           unsigned em = 0u;
 #pragma unroll
           for (int q = 0; q < 8; q++)
-            if (wv[q] != v && relax(c, wv[q], nmE, &bad)) em |= 1u << q;
+            if (wv[q] != v && relax_rec<LabT, FF, UL>(c, wv[q], nmE)) em |= 1u << q;
           const int cnt = __popc(em);
           const int incl = warp_incl_scan(cnt, lane);
           const int tot = __shfl_sync(FULL, incl, 31);
@@ -400,7 +442,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           unsigned em = 0u;  // slots whose vertex joins the next frontier
 #pragma unroll
           for (int q = 0; q < BATCH; q++)
-            if (wv[q] != v && relax(c, wv[q], nmE, &bad)) em |= 1u << q;  // the diagonal entry is skipped
+            if (wv[q] != v && relax<LabT, FF, UL>(c, wv[q], nmE, &bad)) em |= 1u << q;  // the diagonal entry is skipped
           // one shared atomic per warp for the whole batch
           const int cnt = __popc(em);
           const int incl = warp_incl_scan(cnt, lane);
@@ -429,7 +471,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           for (int e0 = beb; e0 < bee; e0 += 32) {
             const int e = e0 + lane;
             const int w = e < bee ? __ldg(colidx + e) : bv;
-            const int enq = w != bv ? relax(c, w, bnm, &bad) : 0;
+            const int enq = w != bv ? relax<LabT, FF, UL>(c, w, bnm, &bad) : 0;
             append(c, enq, w, lane);
           }
         }
@@ -466,14 +508,23 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       const bool f = i < hiL && (uint32_t)lab[i] < base + 1u + (uint32_t)i;
       cL += __popc(__ballot_sync(FULL, f));
     }
+    // U part: labelled vertices above s (UL), else words of the ub bitmap
+    const uint32_t top = base + (uint32_t)s;  // largest value of this window
     const int ws = (s + 1) >> 5;  // first word that can hold a column > s
-    const int nUW = NW - ws;
+    const int nUW = UL ? n - (s + 1) : NW - ws;
     const int perU = (((nUW + nwarps - 1) / nwarps) + 31) & ~31;
-    const int loU = ws + warp * perU, hiU = min(NW, loU + perU);
+    const int loU = (UL ? s + 1 : ws) + warp * perU, hiU = min(UL ? n : NW, loU + perU);
     int cU = 0;
-    for (int j = loU + lane; j < hiU; j += 32) cU += __popc(ub[j]);
+    if (UL) {
+      for (int i0 = loU; i0 < hiU; i0 += 32) {
+        const int i = i0 + lane;
+        cU += __popc(__ballot_sync(FULL, i < hiU && (uint32_t)lab[i] <= top));
+      }
+    } else {
+      for (int j = loU + lane; j < hiU; j += 32) cU += __popc(ub[j]);
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) cU += __shfl_xor_sync(FULL, cU, o);
+      for (int o = 16; o >= 1; o >>= 1) cU += __shfl_xor_sync(FULL, cU, o);
+    }
     if (lane == 0) { s_wcL[warp] = cL; s_wcU[warp] = cU; }
     __syncthreads();
     if (tid == 0) {
@@ -517,7 +568,18 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         pos += __popc(m);
       }
     }
-    {
+    if (UL) {
+      if (off >= 0) {
+        int pos = s_wcU[warp];
+        for (int i0 = loU; i0 < hiU; i0 += 32) {
+          const int i = i0 + lane;
+          const bool f = i < hiU && (uint32_t)lab[i] <= top;
+          const unsigned m = __ballot_sync(FULL, f);
+          if (f) a.pool[off + nL + 1 + pos + __popc(m & lt)] = (uint32_t)i;
+          pos += __popc(m);
+        }
+      }
+    } else {
       int pos = s_wcU[warp];
       for (int j0 = loU; j0 < hiU; j0 += 32) {
         const int j = j0 + lane;
@@ -568,24 +630,29 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16) {
   return label16 ? max_S_t<uint16_t>(n, smem_limit, 1024) : max_S_t<uint32_t>(n, smem_limit, 1024);
 }
 
-template <typename LabT, bool EB, bool FF, bool ELL>
+template <typename LabT, bool EB, bool FF, bool ELL, bool UL>
 static cudaError_t launch_t(const TravArgs& a, int grid, int block, size_t bytes, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<LabT, EB, FF, ELL>,
+  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<LabT, EB, FF, ELL, UL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  trav_smem_kernel<LabT, EB, FF, ELL><<<grid, block, bytes, st>>>(a);
+  trav_smem_kernel<LabT, EB, FF, ELL, UL><<<grid, block, bytes, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename LabT>
 static cudaError_t launch_l(const TravArgs& a, int grid, int block, size_t bytes, cudaStream_t st) {
   const bool ff = a.fill_first != 0;
-  if (a.ell) return ff ? launch_t<LabT, false, true, true>(a, grid, block, bytes, st)
-                       : launch_t<LabT, false, false, true>(a, grid, block, bytes, st);
-  if (a.expand_mode == 2) return ff ? launch_t<LabT, true, true, false>(a, grid, block, bytes, st)
-                                    : launch_t<LabT, true, false, false>(a, grid, block, bytes, st);
-  return ff ? launch_t<LabT, false, true, false>(a, grid, block, bytes, st)
-            : launch_t<LabT, false, false, false>(a, grid, block, bytes, st);
+  if (a.ell) {
+    // U entries by labels when every vertex has a label slot
+    if (a.S >= a.n) return ff ? launch_t<LabT, false, true, true, true>(a, grid, block, bytes, st)
+                              : launch_t<LabT, false, false, true, true>(a, grid, block, bytes, st);
+    return ff ? launch_t<LabT, false, true, true, false>(a, grid, block, bytes, st)
+              : launch_t<LabT, false, false, true, false>(a, grid, block, bytes, st);
+  }
+  if (a.expand_mode == 2) return ff ? launch_t<LabT, true, true, false, false>(a, grid, block, bytes, st)
+                                    : launch_t<LabT, true, false, false, false>(a, grid, block, bytes, st);
+  return ff ? launch_t<LabT, false, true, false, false>(a, grid, block, bytes, st)
+            : launch_t<LabT, false, false, false, false>(a, grid, block, bytes, st);
 }
 
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st) {
@@ -595,7 +662,7 @@ cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16
 
 int trav_smem_static_bytes() {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t, false, false, false>) != cudaSuccess) {
+  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t, false, false, false, false>) != cudaSuccess) {
     cudaGetLastError();
     return 1024;
   }
@@ -603,8 +670,8 @@ int trav_smem_static_bytes() {
 }
 
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16) {
-  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t, false, false, true>
-                          : (const void*)trav_smem_kernel<uint32_t, false, false, true>;
+  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t, false, false, true, true>
+                          : (const void*)trav_smem_kernel<uint32_t, false, false, true, true>;
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
