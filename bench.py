@@ -289,7 +289,7 @@ def main():
     achieved = alg / t_trav / 1e9
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
+    if os.path.exists(tr_path) and not extra:  # counters were taken with the default options
         try:
             traffic = json.load(open(tr_path)).get(name)
         except Exception:
