@@ -136,7 +136,7 @@ def run_reference(args, rank, world):
         return 0
     k, name = WORKLOADS[args.workload]
     A = synth.config(k)
-    stride = 16 if args.workload == "grid3d" else 1
+    stride = 4 if args.workload == "grid3d" else 1
     for _ in range(args.warmup):
         cpu_baseline(A, stride * 4)
     vals, rows = [], []
@@ -295,6 +295,11 @@ def main():
         except Exception:
             traffic = None
 
+    # the dominant traversal tier of this matrix
+    if stats0["ms_traverse_global"] > stats0["ms_traverse_smem"]:
+        kernel_name = "trav_global_kernel (class-ordered maxId traversal, one warp per source) + trav_smem_kernel"
+    else:
+        kernel_name = "trav_smem_kernel (maxId traversal, one CTA per source)"
     line = {
         "metric": "nnz(L+U)/s", "value": value, "unit": "nnz(L+U)/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
@@ -306,17 +311,18 @@ def main():
         "wall_s": wall,
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "trav_smem_kernel (maxId traversal)",
+        "roofline": {"bound": "hbm", "kernel": kernel_name,
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "peak_source": f"{peak_src} (copy bandwidth, burst)", "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg, "ms_per_launch": t_trav * 1000.0},
         "clocks": clocks,
-        "stats": {k2: stats0[k2] for k2 in ("ms_validate", "ms_traverse", "ms_supernode", "ms_emit", "ms_total",
+        "stats": {k2: stats0[k2] for k2 in ("ms_validate", "ms_traverse", "ms_traverse_smem", "ms_traverse_global",
+                                            "ms_supernode", "ms_emit", "ms_total",
                                             "vertices_expanded", "edges_scanned", "pool_retries")},
         "oracle_min_work": {"vscan": int(orc["vscan"].sum()), "escan": int(orc["escan"].sum())},
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, 2 if args.workload == "grid3d" else 1)
+        line["cpu_baseline"] = cpu_baseline(A, 1)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -397,7 +403,7 @@ def run_batch_bench(args, rank, world, local):
             t0 = time.perf_counter()
             dm = [(a.to(dev, non_blocking=True), b.to(dev, non_blocking=True)) for a, b in hmats]
             res = gs.batch_device(dm, opts=opts)
-            outs = [r.to_host() for r in res]
+            outs = gs.results_to_host(res)
             ts.append(time.perf_counter() - t0)
             d2h = sum(8 * (o.n + 1) * 2 + 4 * (o.nnz_L + o.nnz_U) + 4 * o.n + 4 * (o.n_super + 1) for o in outs)
             del res, outs

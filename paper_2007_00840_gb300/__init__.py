@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import GsofaError, gsofa_options, gsofa_result
 
 __all__ = ["options", "symbolic_device", "symbolic_host", "batch_device", "row_counts_noalloc", "Server",
-           "DeviceResult", "HostResult", "GsofaError", "load", "version"]
+           "DeviceResult", "HostResult", "results_to_host", "GsofaError", "load", "version"]
 
 load = _lib.load
 
@@ -94,9 +94,25 @@ class DeviceResult:
         self._owner = own
 
     def to_host(self) -> "HostResult":
-        return HostResult(self.n, self.L_rowptr.cpu().numpy(), self.L_colidx.cpu().numpy(),
-                          self.U_rowptr.cpu().numpy(), self.U_colidx.cpu().numpy(),
-                          self.fill_count.cpu().numpy(), self.super_start.cpu().numpy(), self.stats)
+        return results_to_host([self])[0]
+
+
+def results_to_host(results) -> list:
+    """Copy device results to host arrays: one asynchronous copy per array into
+    pinned memory on the current stream, then one synchronisation for all."""
+    import torch
+    names = ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start")
+    staged = []
+    for r in results:
+        hs = []
+        for nm in names:
+            a = getattr(r, nm)
+            h = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
+            h.copy_(a, non_blocking=True)
+            hs.append(h)
+        staged.append(hs)
+    torch.cuda.current_stream().synchronize()
+    return [HostResult(r.n, *[h.numpy() for h in hs], r.stats) for r, hs in zip(results, staged)]
 
 
 class HostResult:
