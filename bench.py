@@ -61,6 +61,27 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t: float, world: int, device) -> float:
+    """Largest value of t over the ranks (the timed region of the slowest replica).
+    Replicas share nothing else: this is the only cross-rank operation."""
+    if world <= 1:
+        return t
+    import torch
+    x = torch.tensor([t], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+    return float(x.item())
+
+
+def sum_over_ranks(x: float, world: int, device) -> float:
+    """Sum of x over the ranks (whole-job totals of independent replicas)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
 def algorithmic_bytes(vscan, escan, nnz_rows, n):
     """Per-row minimum work of a fill-path search (oracle counts) summed over rows:
     8 B per expanded vertex (two row pointers), 4 B column + 4 B maxId per scanned
@@ -232,10 +253,7 @@ def main():
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     t_dev = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
+    t_dev = max_over_ranks(t_dev, world, dev)
     value = world * args.steps * nnz_step / t_dev
     rows_per_s = world * args.steps * n / t_dev
 
@@ -257,10 +275,7 @@ def main():
             nsup = raw.n_super
             gs.free_raw(raw)
         te = sum(ts)
-        if world > 1:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, world, dev)
         h2d = 4 * (n + 1) + 4 * A.nnz
         d2h = 16 * (n + 1) + 4 * nnz_h + 4 * n + 4 * (nsup + 1)
         e2e = {"value": world * args.steps * nnz_h / te, "unit": "nnz(L+U)/s",
@@ -389,10 +404,7 @@ def run_batch_bench(args, rank, world, local):
     torch.cuda.synchronize(dev)
     clocks = sampler.stop() if sampler else None
     t = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1000.0
-    if world > 1:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, world, dev)
     # end to end: pinned host CSRs in, every result array back to the host
     e2e = None
     if not args.no_e2e:
@@ -408,7 +420,8 @@ def run_batch_bench(args, rank, world, local):
             d2h = sum(8 * (o.n + 1) * 2 + 4 * (o.nnz_L + o.nnz_U) + 4 * o.n + 4 * (o.n_super + 1) for o in outs)
             del res, outs
         h2d = sum(4 * (A.n + 1) + 4 * A.nnz for A in mats)
-        e2e = {"value": world * len(ts) * nnz / sum(ts), "unit": "nnz(L+U)/s", "h2d_bytes_per_step": h2d,
+        te = max_over_ranks(sum(ts), world, dev)
+        e2e = {"value": world * len(ts) * nnz / te, "unit": "nnz(L+U)/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * sum(ts) / len(ts)}
     if rank != 0:
         return 0
@@ -454,6 +467,8 @@ def run_served_bench(args, rank, world, local):
     from paper_2007_00840_gb300 import build as gbuild
     import synth
     torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     gbuild.build()
     dev = torch.device("cuda", local)
     small = synth.config(3)
@@ -535,8 +550,46 @@ def run_served_bench(args, rank, world, local):
     clocks = sampler.stop()
     st = srv.stats()
     srv.close()
+    # end to end: a shorter stream at the same rate with host CSR in and every
+    # result array copied back to the host
+    e2e = None
+    if not args.no_e2e:
+        ne = min(2000, nreq)
+        hpool = [(torch.from_numpy(A.rowptr).pin_memory().numpy(), torch.from_numpy(A.colidx).pin_memory().numpy())
+                 for A in pool]
+        srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30, opts=gs.options())
+        h2d = d2h = nnz_e = 0
+        tickets = []
+        start = time.perf_counter()
+        for i in range(ne):
+            due = start + arrivals[i]
+            while time.perf_counter() < due:
+                pass
+            k = int(which[i])
+            tickets.append(srv.submit(*hpool[k]))
+            h2d += 4 * (pool[k].n + 1) + 4 * pool[k].nnz
+        for t in tickets:
+            r, _ = srv.wait(t)
+            h = r.to_host()
+            nnz_e += h.nnz_L + h.nnz_U
+            d2h += 16 * (h.n + 1) + 4 * (h.nnz_L + h.nnz_U) + 4 * h.n + 4 * (h.n_super + 1)
+            del r
+        te = time.perf_counter() - start
+        srv.close()
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": sum_over_ranks(nnz_e, world, dev) / te, "unit": "nnz(L+U)/s",
+               "h2d_bytes_per_step": h2d / ne, "d2h_bytes_per_step": d2h / ne, "requests": ne,
+               "note": "per request: host CSR submitted, result copied back"}
+    span = max_over_ranks(st["span_s"], world, dev)
+    total_nnz = sum_over_ranks(st["total_nnz"], world, dev)
+    total_rows = sum_over_ranks(st["total_rows"], world, dev)
+    completed = sum_over_ranks(st["completed"], world, dev)
+    launches_all = sum_over_ranks(st["kernel_launches"], world, dev)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
     line = {
-        "metric": "nnz(L+U)/s", "value": st["total_nnz"] / st["span_s"], "unit": "nnz(L+U)/s", "n_gpus": 1,
+        "metric": "nnz(L+U)/s", "value": total_nnz / span, "unit": "nnz(L+U)/s", "n_gpus": world,
         "steps": nreq, "warmup": 2, "ms_per_step": 1000 * st["span_s"] / nreq, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
         "config": {"workload": "served_poisson_mix", "requests": nreq, "rate_per_s": lam,
@@ -544,12 +597,15 @@ def run_served_bench(args, rank, world, local):
                            f"{1000 * t_small:.3f} ms/request, large alone {1000 * t_big:.1f} ms)",
                    "batched_small_req_per_s": batched_rps, "big_fraction": 0.02,
                    "mem_cap_bytes": 150 << 30, "streams": 2, "max_batch": 512},
-        "requests_per_s": st["completed"] / st["span_s"], "rows_per_s": st["total_rows"] / st["span_s"],
+        "requests_per_s": completed / span, "rows_per_s": total_rows / span, "e2e": e2e,
+        "gpu_launches": int(launches_all), "latency_scope": "rank 0" if world > 1 else "all requests",
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "batches": st["batches"],
         "peak_projected_mem_bytes": st["peak_mem_in_use"], "completed": st["completed"], "failed": st["failed"],
         "checked_against_alone": len(check_idx), "mismatches": mismatches, "wall_s": wall, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

@@ -204,7 +204,8 @@ typedef struct gsofa_server_config {
 
 typedef struct gsofa_server_stats {
     int64_t completed, failed, batches, pending;
-    int32_t inflight, pad;
+    int32_t inflight;
+    int32_t kernel_launches;     /* library kernels launched for completed batches (saturates) */
     int64_t total_nnz;           /* nnz(L+U) of completed requests */
     int64_t total_rows;          /* rows of completed requests */
     int64_t mem_in_use, peak_mem_in_use;   /* projected bytes of admitted requests */

@@ -98,7 +98,7 @@ class gsofa_server_stats(ctypes.Structure):
         ("batches", ctypes.c_int64),
         ("pending", ctypes.c_int64),
         ("inflight", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int32),
         ("total_nnz", ctypes.c_int64),
         ("total_rows", ctypes.c_int64),
         ("mem_in_use", ctypes.c_int64),

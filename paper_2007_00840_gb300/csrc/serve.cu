@@ -67,7 +67,7 @@ struct gsofa_server {
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
   // statistics
-  int64_t completed = 0, failed = 0, batches = 0, total_nnz = 0, total_rows = 0;
+  int64_t completed = 0, failed = 0, batches = 0, total_nnz = 0, total_rows = 0, launches = 0;
   int64_t peak_in_use = 0;
   std::vector<float> lat_ms;
   bool have_first = false;
@@ -155,6 +155,7 @@ void worker_loop(gsofa_server* S, int slot) {
       }
     std::lock_guard<std::mutex> lk(S->mu);
     S->batches++;
+    if (rc == GSOFA_OK && k > 0) S->launches += outs[0].stats.kernel_launches;  // the batch's total
     for (int i = 0; i < k; i++) {
       Request* r = take[i];
       r->t_done = now;
@@ -323,6 +324,7 @@ int gsofa_server_get_stats(gsofa_server* S, gsofa_server_stats* st) {
   st->batches = S->batches;
   st->pending = (int64_t)S->pending.size();
   st->inflight = S->inflight;
+  st->kernel_launches = (int32_t)std::min<int64_t>(S->launches, INT32_MAX);
   st->total_nnz = S->total_nnz;
   st->total_rows = S->total_rows;
   st->mem_in_use = S->in_use;
