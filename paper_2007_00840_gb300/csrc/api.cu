@@ -190,6 +190,34 @@ void pfree(T*& p, cudaStream_t st) {
 // Bytes of one global-tier slot of capacity cap (a multiple of 1024 vertices).
 int64_t slot_bytes(int64_t cap) { return cap * 16 + 2 * (cap / 8 + cap / 256); }
 
+// Memory for global-tier slots: half of the caller's budget, else half of the
+// device memory that is free or already held by slots, at most 96 GiB.
+int64_t global_budget(const Ctx* c, const gsofa_options& o) {
+  if (o.mem_budget_bytes > 0) return o.mem_budget_bytes / 2;
+  int64_t b = (int64_t)96 << 30;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    const int64_t held = c->g_lab ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
+    const int64_t half = ((int64_t)fr + held) / 2;
+    if (half < b) b = half;
+  } else {
+    cudaGetLastError();
+  }
+  return b;
+}
+
+// Slots (one warp each) of the global tier for order n: 32 per SM, within the
+// budget, at most 4 per CTA allowed by max_ctas.
+int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o) {
+  const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
+  int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * 32;
+  const int64_t fit = global_budget(c, o) / slot_bytes(cap);
+  if (slots > fit) slots = fit;
+  if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * GLOBAL_WARPS_PER_CTA)
+    slots = (int64_t)o.max_ctas * GLOBAL_WARPS_PER_CTA;
+  return slots;
+}
+
 // Make sure the global-tier slots hold `slots` x `cap` vertices.  Caller holds gmu.
 int ensure_slots(Ctx* c, int64_t cap, int slots, cudaStream_t st) {
   cap = (cap + 1023) / 1024 * 1024;
@@ -336,15 +364,10 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   }
   if (S < n) {
     // one warp per source; as many warps as 32 per SM, within the memory budget
-    const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
-    const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes / 2 : ((int64_t)16 << 30);
-    int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * 32;
-    const int64_t fit = budget / slot_bytes(cap);
-    if (slots > fit) slots = fit;
-    if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * 16) slots = (int64_t)o.max_ctas * 16;
+    const int64_t slots = global_slots(c, n, o);
     if (slots < 1) return GSOFA_E_NOMEM;
-    p->glob_block = 512;
-    p->glob_grid = (int)slots;  // slots (warps); the launch uses ceil(slots / 16) CTAs
+    p->glob_block = 32 * GLOBAL_WARPS_PER_CTA;
+    p->glob_grid = (int)slots;  // slots (warps); small CTAs spread any slot count over every SM
   }
   return GSOFA_OK;
 }
@@ -509,7 +532,8 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
         a.g_cap = c->g_cap;
         a.g_slots = plan.glob_grid;
       }
-      LK(launch_trav_global(a, (plan.glob_grid + 15) / 16, plan.glob_block, st));
+      LK(launch_trav_global(a, (plan.glob_grid + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
+                            plan.glob_block, st));
       CK(cudaEventRecord(c->g_done, st));
     }
     ev.rec(3, st);
@@ -861,7 +885,9 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
     a.g_base = p.c_base;
     a.g_cap = p.c_cap;
     a.g_slots = p.shape.slots;
-    if ((e = launch_trav_global(a, (p.shape.slots + 15) / 16, 512, st)) != cudaSuccess) return e;
+    if ((e = launch_trav_global(a, (p.shape.slots + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
+                                32 * GLOBAL_WARPS_PER_CTA, st)) != cudaSuccess)
+      return e;
   } else if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) {
     return e;
   }
@@ -1391,6 +1417,16 @@ int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, c
   Ctx* c = get_ctx(&err);
   if (!c) return err;
   return run_batch(c, count, n, rp, ci, o, st, outs, true);
+}
+
+int64_t global_tier_bytes(int32_t n, const gsofa_options* opts) {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return 0;
+  gsofa_options o;
+  if (check_options(opts, &o) != GSOFA_OK) gsofa_default_options(&o);
+  const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
+  return global_slots(c, n, o) * slot_bytes(cap);
 }
 
 int device_sms() {

@@ -20,6 +20,9 @@ enum : int32_t {
 
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
+// Warps (= sources in flight) per CTA of the global-tier kernel: small CTAs so
+// that any slot count spreads over every SM.
+constexpr int GLOBAL_WARPS_PER_CTA = 4;
 
 // Counters in one small device block so one copy brings them back.
 struct DevCounters {
@@ -151,6 +154,8 @@ cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream
 int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
                     const gsofa_options* opt, cudaStream_t st, gsofa_result* outs);
 int device_sms();
+// Bytes of the global-tier slots a single-matrix call of order n would hold.
+int64_t global_tier_bytes(int32_t n, const gsofa_options* opts);
 void detach_result_stream(gsofa_result* r);
 int32_t smem_tier_max_order();
 int wait_stream(cudaStream_t st);  // bounded wait; GSOFA_OK / GSOFA_E_TIMEOUT / GSOFA_E_CUDA

@@ -83,7 +83,7 @@ int64_t projected_bytes(const gsofa_server* S, int32_t n, int64_t nnz, bool host
   const int64_t full = (int64_t)n * ((int64_t)n + 1);
   if (est > full) est = full;
   int64_t b = csr + rows + 8 * est + (1 << 20);                // row pool + L/U outputs
-  if (n > S->smem_max_n) b += (12 * (int64_t)n + (int64_t)n / 4) * (int64_t)S->sms;  // global-tier slots
+  if (n > S->smem_max_n) b += global_tier_bytes(n, &S->cfg.opts);  // global-tier slots, as a call would size them
   return b;
 }
 
