@@ -376,13 +376,24 @@ def run_batch_bench(args, rank, world, local):
     dev = torch.device("cuda", local)
     dmats = [(torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev)) for A in mats]
     rows = sum(A.n for A in mats)
-    opts = gs.options(collect_stats=1, autotune=1)
+    extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
+    opts = gs.options(**{"collect_stats": 1, "autotune": 1, **extra})
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    import tempfile
+    tune_file = os.path.join(tempfile.mkdtemp(prefix="gsofa_tune_"), "shapes.txt")
+    os.environ["GSOFA_TUNE_FILE"] = tune_file  # the autotuner appends the shape it picks
     for _ in range(max(args.warmup, 1)):
         res = gs.batch_device(dmats, opts=opts)
         del res
     torch.cuda.synchronize(dev)
+    tuned = None
+    if os.path.exists(tune_file):
+        f = open(tune_file).read().split()
+        if len(f) >= 7:
+            tuned = {"threads_per_source": int(f[1]), "ctas_per_sm": int(f[2]), "list_capacity": int(f[3]),
+                     "work_chunk": int(f[4]), "kernel": ["cta_per_source_bfs", "warp_per_source_class"][int(f[5])],
+                     "class_slots": int(f[6])}
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -410,10 +421,15 @@ def run_batch_bench(args, rank, world, local):
     if not args.no_e2e:
         hmats = [(torch.from_numpy(A.rowptr).pin_memory(), torch.from_numpy(A.colidx).pin_memory()) for A in mats]
         ts = []
+        # device staging buffers reused every step (as a pipeline would), so the
+        # batch plan and its captured graph are reused too
+        dm = [(torch.empty_like(a, device=dev), torch.empty_like(b, device=dev)) for a, b in hmats]
         for it in range(1 + max(1, args.steps // 2)):  # the first pass (pinned host blocks) is not timed
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            dm = [(a.to(dev, non_blocking=True), b.to(dev, non_blocking=True)) for a, b in hmats]
+            for (da, db), (a, b) in zip(dm, hmats):
+                da.copy_(a, non_blocking=True)
+                db.copy_(b, non_blocking=True)
             res = gs.batch_device(dm, opts=opts)
             outs = gs.results_to_host(res)
             if it > 0:
@@ -446,6 +462,7 @@ def run_batch_bench(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
         "config": {"workload": "batch512_mix", "matrices": len(mats), "rows": rows, "nnz_LU": int(nnz),
+                   "options": extra, "tuned_shape": tuned,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "rows_per_s": world * args.steps * rows / t, "matrices_per_s": world * args.steps * len(mats) / t,
         "e2e": e2e, "gpu_launches": launches,

@@ -478,8 +478,8 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   if (plan.S > 0) {
     spill_cap = plan.S > plan.list_cap ? plan.S - plan.list_cap : 1;
     CK(palloc(c, &spill, (size_t)plan.smem_grid * 2 * (size_t)spill_cap, st));
-    if (o.expand_mode == 0 || o.expand_mode == 3) CK(palloc(c, &ell, (size_t)n, st));
   }
+  if (n > 0 && (o.expand_mode == 0 || o.expand_mode == 3)) CK(palloc(c, &ell, (size_t)n, st));
   // order: shared tier [S-1 .. 0] then global tier [n-1 .. S] (largest source first)
   LK(launch_iota_desc(order, plan.S, plan.S, st));
   LK(launch_iota_desc(order + plan.S, n, n - plan.S, st));
@@ -519,6 +519,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     if (plan.S < n) {
       a.order = order + plan.S;
       a.nsrc = n - plan.S;
+      a.ell = ell;
       {
         const int64_t capW = c->g_cap / 32, capS = capW / 32, slots = c->g_slots;
         a.g_lab = c->g_lab;
@@ -696,6 +697,7 @@ struct BatchPlan {
   int32_t* spill = nullptr;
   int64_t spill_cap = 0;
   int64_t spill_alloc = 0;
+  int4* ell = nullptr;              // ELL records of every row (row_base + v)
   // class-ordered tier slots (kernel 1)
   uint32_t* c_lab = nullptr;
   int32_t* c_queue = nullptr;
@@ -722,7 +724,7 @@ void free_plan(BatchPlan* p) {
     for (void* q : {(void*)p->d_mats, (void*)p->d_item_start, (void*)p->d_mat_order, (void*)p->d_ctr,
                     (void*)p->row_off, (void*)p->row_nL, (void*)p->row_nU, (void*)p->flags, (void*)p->fill,
                     (void*)p->pool, (void*)p->spill, (void*)p->c_lab, (void*)p->c_queue, (void*)p->c_list,
-                    (void*)p->c_bits, (void*)p->c_base})
+                    (void*)p->c_bits, (void*)p->c_base, (void*)p->ell})
       if (q) cudaFreeAsync(q, p->stream);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -748,6 +750,7 @@ void free_plan(BatchPlan* p) {
   cudaFree(p->c_list);
   cudaFree(p->c_bits);
   cudaFree(p->c_base);
+  cudaFree(p->ell);
   if (p->h_ctr) cudaFreeHost(p->h_ctr);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
@@ -783,10 +786,11 @@ void load_tune_file(BatchCache& bc) {
   FILE* fp = std::fopen(f, "r");
   if (!fp) return;
   unsigned long long key;
-  int block, occ, cap, chunk;
-  while (std::fscanf(fp, "%llx %d %d %d %d", &key, &block, &occ, &cap, &chunk) == 5) {
+  int block, occ, cap, chunk, kernel, slots;
+  while (std::fscanf(fp, "%llx %d %d %d %d %d %d", &key, &block, &occ, &cap, &chunk, &kernel, &slots) == 7) {
     LaunchShape sh;
     sh.block = block; sh.occ = occ; sh.list_cap = cap; sh.work_chunk = chunk;
+    sh.kernel = kernel; sh.slots = slots;
     bc.tuned[key] = sh;
   }
   std::fclose(fp);
@@ -797,7 +801,10 @@ void save_tune_entry(uint64_t key, const LaunchShape& sh) {
   if (!f) return;
   FILE* fp = std::fopen(f, "a");
   if (!fp) return;
-  std::fprintf(fp, "%llx %d %d %d %d\n", (unsigned long long)key, sh.block, sh.occ, sh.list_cap, sh.work_chunk);
+  // key, threads per source, CTAs per SM, list capacity, work chunk, kernel (0 CTA per
+  // source, 1 class-ordered warp per source), class-kernel slots
+  std::fprintf(fp, "%llx %d %d %d %d %d %d\n", (unsigned long long)key, sh.block, sh.occ, sh.list_cap,
+               sh.work_chunk, sh.kernel, sh.slots);
   std::fclose(fp);
 }
 
@@ -867,7 +874,12 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.nmats = p.B;
   a.chunk = p.shape.work_chunk;
   a.mat_tot = p.mat_tot();
-  a.expand_mode = (o.expand_mode == 0 || o.expand_mode == 3) ? 1 : o.expand_mode;
+  a.expand_mode = (o.expand_mode == 0 || o.expand_mode == 3) ? 3 : o.expand_mode;
+  if (a.expand_mode == 3) {
+    // adjacency records of every member (both traversal kernels read them)
+    if ((e = launch_build_ell_batch(p.d_mats, p.B, p.N, p.ell, p.ctr(), st)) != cudaSuccess) return e;
+    a.ell = p.ell;
+  }
   // while capturing, external records become event nodes of the graph
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
@@ -1058,7 +1070,8 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
               palloc(c, &p->row_nU, (size_t)p->N, st) == cudaSuccess &&
               palloc(c, &p->flags, (size_t)p->N, st) == cudaSuccess &&
               palloc(c, &p->fill, (size_t)p->N, st) == cudaSuccess &&
-              palloc(c, &p->pool, (size_t)p->pool_cap, st) == cudaSuccess;
+              palloc(c, &p->pool, (size_t)p->pool_cap, st) == cudaSuccess &&
+              palloc(c, &p->ell, (size_t)(p->N > 0 ? p->N : 1), st) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       p->h_ctr = nullptr;
@@ -1089,6 +1102,7 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
             cudaMalloc(&p->flags, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
             cudaMalloc(&p->fill, sizeof(int32_t) * (size_t)p->N) == cudaSuccess &&
             cudaMalloc(&p->pool, sizeof(uint32_t) * (size_t)p->pool_cap) == cudaSuccess &&
+            cudaMalloc(&p->ell, sizeof(int4) * (size_t)(p->N > 0 ? p->N : 1)) == cudaSuccess &&
             cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -1328,6 +1342,8 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
   sig = mix64(sig, ((uint64_t)o.chunk_size << 32) ^ ((uint64_t)o.fill_first << 8) ^ (uint64_t)o.validate);
   sig = mix64(sig, ((uint64_t)o.work_chunk << 32) ^ ((uint64_t)o.list_capacity << 4) ^ (uint64_t)o.threads_per_source);
   sig = mix64(sig, ((uint64_t)o.collect_stats << 32) ^ (uint64_t)o.max_ctas);
+  sig = mix64(sig, ((uint64_t)o.frontier_order << 48) ^ ((uint64_t)o.expand_mode << 32) ^
+                       ((uint64_t)o.label_bits << 16) ^ (uint64_t)o.autotune);
   std::unique_lock<std::mutex> lk(bc.mu);  // cached plans are used by one call at a time
   load_tune_file(bc);
   BatchPlan* p = nullptr;

@@ -542,34 +542,61 @@ cudaError_t launch_compact_long(int64_t nrows, const uint32_t* pool, const int64
 // traversal skips).  Rows with more entries or offsets beyond +-32767 get the
 // marker -32768 in slot 0 and are read from the CSR instead.
 namespace gsofa {
+// ELL record of row v: up to 8 off-diagonal neighbours as 16-bit offsets w - v,
+// zero-padded; rows that do not fit (more than 8 neighbours, an offset beyond
+// +-32767, or a column out of range, possible only when validation is skipped)
+// get the sentinel -32768 in slot 0 and are read from the CSR, which checks them.
+__device__ int4 ell_record(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int32_t n,
+                           long long v) {
+  const int rb = rowptr[v], re = rowptr[v + 1];
+  short off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int k = 0;
+  bool fits = true;
+  for (int e = rb; e < re; e++) {
+    const int w = colidx[e];
+    const long long d = (long long)w - v;
+    if (d == 0) continue;
+    if (k == 8 || d > 32767 || d < -32767 || w < 0 || w >= n) { fits = false; break; }
+    off[k++] = (short)d;
+  }
+  if (!fits) {
+    off[0] = (short)-32768;
+    for (int q = 1; q < 8; q++) off[q] = 0;
+  }
+  int4 r;
+  r.x = (int)(((unsigned)(unsigned short)off[1] << 16) | (unsigned short)off[0]);
+  r.y = (int)(((unsigned)(unsigned short)off[3] << 16) | (unsigned short)off[2]);
+  r.z = (int)(((unsigned)(unsigned short)off[5] << 16) | (unsigned short)off[4]);
+  r.w = (int)(((unsigned)(unsigned short)off[7] << 16) | (unsigned short)off[6]);
+  return r;
+}
+
 __global__ void build_ell_kernel(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                  int4* __restrict__ ell, DevCounters* ctr) {
   if (input_error(ctr)) return;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const int rb = rowptr[v], re = rowptr[v + 1];
-    short off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int k = 0;
-    bool fits = true;
-    for (int e = rb; e < re; e++) {
-      const int w = colidx[e];
-      const long long d = (long long)w - v;
-      if (d == 0) continue;
-      // out-of-range columns (possible only when validation is skipped) go to the
-      // CSR path, which checks them
-      if (k == 8 || d > 32767 || d < -32767 || w < 0 || w >= n) { fits = false; break; }
-      off[k++] = (short)d;
-    }
-    if (!fits) {
-      off[0] = (short)-32768;
-      for (int q = 1; q < 8; q++) off[q] = 0;
-    }
-    int4 r;
-    r.x = (int)(((unsigned)(unsigned short)off[1] << 16) | (unsigned short)off[0]);
-    r.y = (int)(((unsigned)(unsigned short)off[3] << 16) | (unsigned short)off[2]);
-    r.z = (int)(((unsigned)(unsigned short)off[5] << 16) | (unsigned short)off[4]);
-    r.w = (int)(((unsigned)(unsigned short)off[7] << 16) | (unsigned short)off[6]);
-    ell[v] = r;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    ell[v] = ell_record(rowptr, colidx, n, v);
+}
+
+// Records of every row of a batch, indexed by the row's global index (row_base + v).
+__global__ void build_ell_batch_kernel(const MatDesc* __restrict__ mats, int32_t nmats, long long total_rows,
+                                       int4* __restrict__ ell, DevCounters* ctr) {
+  if (input_error(ctr)) return;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total_rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    const MatDesc d = mats[mat_of_row(mats, nmats, r)];
+    ell[r] = ell_record(d.rowptr, d.colidx, d.n, r - d.row_base);
   }
+}
+
+cudaError_t launch_build_ell_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows, int4* ell,
+                                   DevCounters* ctr, cudaStream_t st) {
+  if (total_rows <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = (total_rows + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  build_ell_batch_kernel<<<(int)grid, block, 0, st>>>(mats, nmats, total_rows, ell, ctr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ell, DevCounters* ctr,

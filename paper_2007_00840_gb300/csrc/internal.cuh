@@ -148,6 +148,8 @@ cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t s
 cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
 cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ell, DevCounters* ctr,
                              cudaStream_t st);
+cudaError_t launch_build_ell_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows, int4* ell,
+                                   DevCounters* ctr, cudaStream_t st);
 cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
 
 // host helpers (api.cu)

@@ -51,6 +51,26 @@ __device__ __forceinline__ void set_bit2(uint32_t* W, uint32_t* S, int v) {
   if (old == 0u) atomicOr(&S[v >> 10], 1u << ((v >> 5) & 31));
 }
 
+// Fire-and-forget variant of set_bit2 (reductions, no return): the word and its
+// summary bit are both set; a summary bit over a word that already had bits is
+// harmless.  Visible to the warp's later reads after __syncwarp.
+__device__ __forceinline__ void red_bit2(uint32_t* W, uint32_t* S, int v) {
+  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(W + (v >> 5)), "r"(1u << (v & 31)) : "memory");
+  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(S + (v >> 10)), "r"(1u << ((v >> 5) & 31)) : "memory");
+}
+
+// Global atomic minimum issued under a predicate; 0xFFFFFFFF when not issued.
+// Written as a predicated instruction so that the 8 slots of a record are in
+// flight together instead of one after another behind branches.
+__device__ __forceinline__ uint32_t gmin_if(uint32_t* p, uint32_t v, bool pred) {
+  uint32_t r = 0xFFFFFFFFu;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.global.min.u32 %0, [%1], %2;\n\t}"
+               : "+r"(r)
+               : "l"(p), "r"(v), "r"((uint32_t)pred)
+               : "memory");
+  return r;
+}
+
 // Smallest set bit of P at a position in [from, s); -1 if none.  Warp-wide.
 __device__ int next_pending(const Slot& sl, int from, int s, int lane) {
   if (from >= s) return -1;
@@ -95,6 +115,31 @@ __device__ __forceinline__ int relax_class(const Slot& sl, int w, int s, int t, 
     set_bit2(sl.P, sl.PS, w);           // a fill of L(s,:); its own class later
   }
   return 0;
+}
+
+// Relax the (up to 8) neighbours of one vertex read from its ELL record for
+// class t: w = v + offset, in [0, n) by construction of the records, empty
+// slots hold w == v.  The label updates are issued together; vertices above s
+// are U entries, lowered vertices above t are pending fills (their own class
+// later).  Returns the slots whose vertex joins class t.
+__device__ __forceinline__ unsigned relax8_class(const Slot& sl, const int (&wv)[8], int v, int s, int t,
+                                                 uint32_t pE) {
+  uint32_t old[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) old[q] = gmin_if(&sl.lab[wv[q] < 0 ? 0 : wv[q]], pE, wv[q] != v && wv[q] < s);
+  unsigned em = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int w = wv[q];
+    if (w == v) continue;
+    if (w > s) {
+      red_bit2(sl.U, sl.US, w);
+    } else if (w < s && old[q] > pE) {  // first reached, now with maxId t
+      if (w < t) em |= 1u << q;          // same class
+      else red_bit2(sl.P, sl.PS, w);     // a fill of L(s,:)
+    }
+  }
+  return em;
 }
 
 }  // namespace
@@ -202,7 +247,65 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
       bool single = true;
       while (qlen > 0) {
         int nq = 0;
-        if (single) {  // one vertex: the lanes share its row
+        if (a.ell) {
+          // one vertex per lane from its ELL record; rows without a record
+          // (sentinel) are walked from the CSR, one lane per row, afterwards
+          for (int i0 = 0; i0 < qlen; i0 += 32) {
+            const int i = i0 + lane;
+            int v = -1;
+            if (i < qlen) v = single ? t : qc[i];
+            uint32_t h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
+            bool fb = false;
+            if (v >= 0) {
+              const int4 r4 = __ldg(a.ell + rowb + v);
+              h0 = (uint32_t)r4.x; h1 = (uint32_t)r4.y; h2 = (uint32_t)r4.z; h3 = (uint32_t)r4.w;
+              fb = (h0 & 0xFFFFu) == 0x8000u;
+              if (fb) h0 = 0u;
+              if (a.collect_stats) {
+                n_exp++;
+                n_edge += (unsigned long long)(__ldg(rowptr + v + 1) - __ldg(rowptr + v));
+              }
+            }
+            int wv[8];
+            wv[0] = v + (int)(short)(h0 & 0xFFFFu); wv[1] = v + (int)(short)(h0 >> 16);
+            wv[2] = v + (int)(short)(h1 & 0xFFFFu); wv[3] = v + (int)(short)(h1 >> 16);
+            wv[4] = v + (int)(short)(h2 & 0xFFFFu); wv[5] = v + (int)(short)(h2 >> 16);
+            wv[6] = v + (int)(short)(h3 & 0xFFFFu); wv[7] = v + (int)(short)(h3 >> 16);
+            const unsigned em = v >= 0 ? relax8_class(sl, wv, v, s, t, pE) : 0u;
+            const int cnt = __popc(em);
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int tt = __shfl_up_sync(FULL, inc, o);
+              if (lane >= o) inc += tt;
+            }
+            int pos = nq + inc - cnt;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+              if ((em >> q) & 1u) qn[pos++] = wv[q];
+            nq += __shfl_sync(FULL, inc, 31);
+            // rows that did not fit a record
+            unsigned fm = __ballot_sync(FULL, fb);
+            while (fm) {
+              const int l = __ffs(fm) - 1;
+              fm &= fm - 1;
+              const int u = __shfl_sync(FULL, v, l);
+              const int eb = __ldg(rowptr + u), ee = __ldg(rowptr + u + 1);
+              for (int e0 = eb; e0 < ee; e0 += 32) {
+                const int e = e0 + lane;
+                int w = 0, enq = 0;
+                if (e < ee) {
+                  w = __ldg(colidx + e);
+                  if (w != u) enq = relax_class(sl, w, s, t, pE, n, &bad);
+                }
+                const unsigned m = __ballot_sync(FULL, enq);
+                if (enq) qn[nq + __popc(m & lt)] = w;
+                nq += __popc(m);
+              }
+            }
+          }
+          single = false;
+        } else if (single) {  // one vertex: the lanes share its row
           const int eb = __ldg(rowptr + t), ee = __ldg(rowptr + t + 1);
           if (lane == 0) { n_exp++; n_edge += (unsigned long long)(ee - eb); }
           for (int e0 = eb; e0 < ee; e0 += 32) {
@@ -256,14 +359,14 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
     int nU = 1;
     for (int sw0 = s_lo; sw0 < ns; sw0 += 32) {
       const int sw = sw0 + lane;
-      const uint32_t m = sw < ns ? sl.US[sw] : 0u;
+      const uint32_t m = sw < ns ? *(volatile uint32_t*)&sl.US[sw] : 0u;
       unsigned any = __ballot_sync(FULL, m != 0u);
       while (any) {
         const int l = __ffs(any) - 1;
         any &= any - 1;
         const uint32_t ml = __shfl_sync(FULL, m, l);
         const int pw = ((sw0 + l) << 5) + lane;
-        const uint32_t word = ((ml >> lane) & 1u) ? sl.U[pw] : 0u;
+        const uint32_t word = ((ml >> lane) & 1u) ? *(volatile uint32_t*)&sl.U[pw] : 0u;
         int c = __popc(word);
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
@@ -295,7 +398,7 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
     long long pos = (long long)off + nL + 1;
     for (int sw0 = s_lo; sw0 < ns; sw0 += 32) {
       const int sw = sw0 + lane;
-      const uint32_t m = sw < ns ? sl.US[sw] : 0u;
+      const uint32_t m = sw < ns ? *(volatile uint32_t*)&sl.US[sw] : 0u;
       unsigned any = __ballot_sync(FULL, m != 0u);
       while (any) {
         const int l = __ffs(any) - 1;
@@ -304,7 +407,7 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
         const int pw = ((sw0 + l) << 5) + lane;
         uint32_t word = 0u;
         if ((ml >> lane) & 1u) {
-          word = sl.U[pw];
+          word = *(volatile uint32_t*)&sl.U[pw];
           sl.U[pw] = 0u;
         }
         const int c = __popc(word);

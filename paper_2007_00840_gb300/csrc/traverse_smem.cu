@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
           bool fb = false;
           int wv[8];
           if (v >= 0) {
-            const int4 r4 = __ldg(a.ell + v);
+            const int4 r4 = __ldg(a.ell + rowb + v);
             const uint32_t h[4] = {(uint32_t)r4.x, (uint32_t)r4.y, (uint32_t)r4.z, (uint32_t)r4.w};
             fb = (h[0] & 0xFFFFu) == 0x8000u;
 #pragma unroll
