@@ -1280,9 +1280,19 @@ int batch_phase2(Ctx* c, BatchPlan* p, const int32_t* n, cudaStream_t st, gsofa_
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) {
       outs[p->members[0]].stats.ms_traverse = ms;
-      outs[p->members[0]].stats.ms_traverse_smem = ms;
+      if (p->shape.kernel == 1) outs[p->members[0]].stats.ms_traverse_global = ms;
+      else outs[p->members[0]].stats.ms_traverse_smem = ms;
     }
     cudaGetLastError();
+  }
+  if (p->B > 0) {  // counters of the batched launch (collect_stats)
+    const DevCounters* h = p->hctr();
+    gsofa_stats& sm = outs[p->members[0]].stats;
+    sm.vertices_expanded = (int64_t)h->expansions;
+    sm.edges_scanned = (int64_t)h->edges;
+    sm.levels = (int64_t)h->levels;
+    sm.cycles_traverse = (int64_t)h->cyc_trav;
+    sm.cycles_emit = (int64_t)h->cyc_emit;
   }
   return GSOFA_OK;
 }
