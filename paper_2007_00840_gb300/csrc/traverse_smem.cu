@@ -167,6 +167,109 @@ __device__ __forceinline__ void append(const Src<LabT>& c, int enq, int w, int l
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// One level of the ELL path when the frontier is small: LPV lanes share a
+// frontier vertex and each relaxes 8 / LPV of its record's slots, so the chain
+// of dependent slot updates a warp walks is LPV times shorter (the level is
+// latency-bound: every warp has at most one round).  Rows without a record are
+// walked from the CSR by the whole warp.
+template <typename LabT, bool FF, bool UL, int LPV>
+__device__ __forceinline__ void small_level(const Src<LabT>& c, const TravArgs& a, const LabT* Lc, const int32_t* Sc,
+                                            uint32_t* Dc, int qc, int CAP, long long rowb, uint32_t base,
+                                            const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                            int warp, int nwarps, int lane, unsigned long long& n_exp,
+                                            unsigned long long& n_edge, int* bad) {
+  constexpr int SPL = 8 / LPV, VPW = 32 / LPV;
+  const int sub = lane & (LPV - 1);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r0 = warp * VPW; r0 < qc; r0 += nwarps * VPW) {
+    const int r = r0 + lane / LPV;
+    int v = -1;
+    uint32_t nmE = 0u;
+    if (r < qc) {
+      v = r < CAP ? (int)Lc[r] : Sc[r - CAP];
+      Dc[v >> 5] = 0u;  // as in the main loop: nothing sets bits of Dc during the level
+      const uint32_t lv = (uint32_t)c.lab[v];
+      const uint32_t vE = base + 1u + (uint32_t)v;
+      nmE = lv > vE ? lv : vE;
+      if (sub == 0) {
+        n_exp++;
+        if (a.collect_stats) n_edge += (unsigned long long)(__ldg(rowptr + v + 1) - __ldg(rowptr + v));
+      }
+    }
+    bool fb = false;
+    uint32_t x0 = 0u, x1 = 0u;  // this lane's record words (SPL = 4: two words; 2: one; 1: half of one)
+    if (v >= 0) {
+      const int4 r4 = __ldg(a.ell + rowb + v);
+      fb = ((uint32_t)r4.x & 0xFFFFu) == 0x8000u;
+      if (!fb) {
+        if (SPL == 4) {
+          x0 = sub ? (uint32_t)r4.z : (uint32_t)r4.x;
+          x1 = sub ? (uint32_t)r4.w : (uint32_t)r4.y;
+        } else {
+          const int wi = SPL == 2 ? sub : (sub >> 1);
+          x0 = wi == 0 ? (uint32_t)r4.x : wi == 1 ? (uint32_t)r4.y : wi == 2 ? (uint32_t)r4.z : (uint32_t)r4.w;
+          if (SPL == 1) x0 = (sub & 1) ? (x0 >> 16) : (x0 & 0xFFFFu);
+        }
+      }
+    }
+    int wv[SPL];
+#pragma unroll
+    for (int q = 0; q < SPL; q++) {
+      const uint32_t x = q < 2 ? x0 : x1;
+      wv[q] = v + (int)(short)((q & 1) ? (x >> 16) : (x & 0xFFFFu));
+    }
+    unsigned em = 0u;
+#pragma unroll
+    for (int q = 0; q < SPL; q++)
+      if (wv[q] != v && relax_rec<LabT, FF, UL>(c, wv[q], nmE)) em |= 1u << q;
+    const int cnt = __popc(em);
+    const int incl = warp_incl_scan(cnt, lane);
+    const int tot = __shfl_sync(FULL, incl, 31);
+    if (tot) {
+      int basep = 0;
+      if (lane == 31) basep = atomicAdd(c.qn, tot);
+      basep = __shfl_sync(FULL, basep, 31);
+      int pos = basep + incl - cnt;
+#pragma unroll
+      for (int q = 0; q < SPL; q++) {
+        if ((em >> q) & 1u) {
+          if (pos < CAP) c.Ln[pos] = (LabT)wv[q]; else c.Sn[pos - CAP] = wv[q];
+          pos++;
+        }
+      }
+    }
+    unsigned fm = __ballot_sync(FULL, fb && sub == 0);
+    while (fm) {
+      const int l = __ffs(fm) - 1;
+      fm &= fm - 1u;
+      const int u = __shfl_sync(FULL, v, l);
+      const uint32_t unm = __shfl_sync(FULL, nmE, l);
+      const int eb = __ldg(rowptr + u), ee = __ldg(rowptr + u + 1);
+      for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + lane;
+        int w = u, enq = 0;
+        if (e < ee) {
+          w = __ldg(colidx + e);
+          if (w != u) enq = relax<LabT, FF, UL>(c, w, unm, bad);
+        }
+        const unsigned m = __ballot_sync(FULL, enq);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          int b2 = 0;
+          if (lane == leader) b2 = atomicAdd(c.qn, __popc(m));
+          b2 = __shfl_sync(FULL, b2, leader);
+          if (enq) {
+            const int p2 = b2 + __popc(m & lt);
+            if (p2 < CAP) c.Ln[p2] = (LabT)w; else c.Sn[p2 - CAP] = w;
+          }
+        }
+      }
+    }
+  }
+}
+
+
+
 }  // namespace
 
 template <typename LabT>
@@ -317,7 +420,18 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       uint32_t* Dc = cb ? D1 : D0;
       Src<LabT> c{lab, ub, nb ? D1 : D0, nb ? L1 : L0, nb ? S1 : S0, &s_q[L % 3], base, s, n, CAP};
       if (tid == 0) s_q[(L + 1) % 3] = 0;
-      for (int r0 = warp * 32; r0 < qc; r0 += nthr) {
+      // small frontier: several lanes per vertex (one round per warp)
+      const int lpv = !ELL ? 1 : qc * 8 <= nthr ? 8 : qc * 4 <= nthr ? 4 : qc * 2 <= nthr ? 2 : 1;
+      if (ELL && lpv == 8)
+        small_level<LabT, FF, UL, 8>(c, a, Lc, Sc, Dc, qc, CAP, rowb, base, rowptr, colidx, warp, nwarps, lane, n_exp,
+                                     n_edge, &bad);
+      else if (ELL && lpv == 4)
+        small_level<LabT, FF, UL, 4>(c, a, Lc, Sc, Dc, qc, CAP, rowb, base, rowptr, colidx, warp, nwarps, lane, n_exp,
+                                     n_edge, &bad);
+      else if (ELL && lpv == 2)
+        small_level<LabT, FF, UL, 2>(c, a, Lc, Sc, Dc, qc, CAP, rowb, base, rowptr, colidx, warp, nwarps, lane, n_exp,
+                                     n_edge, &bad);
+      for (int r0 = warp * 32; lpv == 1 && r0 < qc; r0 += nthr) {
         const int r = r0 + lane;
         int v = -1, eb = 0, ee = 0;
         uint32_t nmE = 0u;
