@@ -466,7 +466,10 @@ def run_batch_bench(args, rank, world, local):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "rows_per_s": world * args.steps * rows / t, "matrices_per_s": world * args.steps * len(mats) / t,
         "e2e": e2e, "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "trav_smem_kernel (batched maxId traversal)", "achieved": alg / t_trav / 1e9,
+        "roofline": {"bound": "hbm", "kernel": ("trav_global_kernel (batched, class-ordered, one warp per source)"
+                                                if tuned and tuned["kernel"] == "warp_per_source_class"
+                                                else "trav_smem_kernel (batched, one CTA per source)"),
+                     "achieved": alg / t_trav / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": alg / t_trav / 1e9 / peak, "traffic": None,
                      "peak_source": f"{src} (copy bandwidth, burst)", "algorithmic_bytes_per_launch": alg,
                      "ms_per_launch": t_trav * 1000},
