@@ -136,18 +136,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(A, stride: int):
-    """The CPU oracle, as it stands, on every `stride`-th row, all host cores."""
+def cpu_baseline(A, stride: int, min_wall: float = 1.0):
+    """The CPU oracle, as it stands, on every `stride`-th row, all host cores;
+    the sample is repeated until it has run for min_wall seconds (a workload of
+    a few milliseconds gives no stable rate alone)."""
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     rows = np.arange(0, A.n, stride, dtype=np.int32)
+    reps, nnz = 0, 0
     t0 = time.perf_counter()
-    r = oracle.symbolic(A, rows=rows, nthreads=cores)
-    dt = time.perf_counter() - t0
-    nnz = int(r["L_rowptr"][-1] + r["U_rowptr"][-1])
+    while True:
+        r = oracle.symbolic(A, rows=rows, nthreads=cores)
+        nnz += int(r["L_rowptr"][-1] + r["U_rowptr"][-1])
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_wall:
+            break
     return {"value": nnz / dt, "unit": "nnz(L+U)/s", "cores": cores, "kind": "oracle",
-            "sample": f"every {stride}th row ({rows.size} of {A.n} rows, {nnz} nnz(L+U)), {dt:.2f} s wall",
-            "rows_per_s": rows.size / dt}
+            "sample": f"every {stride}th row ({rows.size} of {A.n} rows) x {reps} passes, "
+                      f"{nnz} nnz(L+U), {dt:.2f} s wall",
+            "rows_per_s": reps * rows.size / dt}
 
 
 def run_reference(args, rank, world):
@@ -159,11 +167,11 @@ def run_reference(args, rank, world):
     A = synth.config(k)
     stride = 4 if args.workload == "grid3d" else 1
     for _ in range(args.warmup):
-        cpu_baseline(A, stride * 4)
+        cpu_baseline(A, stride * 4, min_wall=0.0)
     vals, rows = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cb = cpu_baseline(A, stride)
+        cb = cpu_baseline(A, stride, min_wall=0.25)
         vals.append(cb["value"])
         rows.append(cb["rows_per_s"])
     wall = time.perf_counter() - t0
