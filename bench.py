@@ -346,6 +346,18 @@ def main():
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, 1)
+        if args.workload in ("grid2d", "grid3d"):
+            # the same oracle on one host core, on a row sample
+            import oracle
+            stride = 8 if args.workload == "grid3d" else 1
+            rows1 = np.arange(0, A.n, stride, dtype=np.int32)
+            t0 = time.perf_counter()
+            r1 = oracle.symbolic(A, rows=rows1, nthreads=1)
+            dt1 = time.perf_counter() - t0
+            nnz1 = int(r1["L_rowptr"][-1] + r1["U_rowptr"][-1])
+            line["cpu_baseline"]["single_thread"] = {
+                "value": nnz1 / dt1, "unit": "nnz(L+U)/s", "cores": 1,
+                "sample": f"every {stride}th row ({rows1.size} rows, {nnz1} nnz(L+U)), {dt1:.2f} s"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
