@@ -21,7 +21,8 @@ def _pool():
     return mats
 
 
-def test_served_equal_alone_and_oracle():
+@pytest.mark.parametrize("streams,max_batch", [(3, 16), (2, 512)])
+def test_served_equal_alone_and_oracle(streams, max_batch):
     import torch
     import paper_2007_00840_gb300 as gs
     pool = _pool()
@@ -32,7 +33,7 @@ def test_served_equal_alone_and_oracle():
         if A.n <= 5000:
             assert_same(h, oracle_full(A))
     rng = np.random.default_rng(11)
-    srv = gs.Server(streams=3, max_batch=16)
+    srv = gs.Server(streams=streams, max_batch=max_batch)
     tickets = []
     for i in range(240):
         k = int(rng.integers(0, len(pool)))
