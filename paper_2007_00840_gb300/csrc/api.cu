@@ -45,6 +45,7 @@ struct Ctx {
   // row-pool size that fitted last time, by matrix order
   std::mutex hmu;
   std::map<int32_t, long long> pool_hint;
+  double rows_ratio = 0.0;  // largest pool entries per row seen (nnz(L+U) + 1 per row)
   // single-matrix autotune: faster frontier order by (n, nnz)
   std::map<std::pair<int32_t, int64_t>, int> order_tuned;
 };
@@ -185,6 +186,30 @@ template <typename T>
 void pfree(T*& p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
   p = nullptr;
+}
+
+// First row-pool size for `rows` rows whose full rows hold at most `full`
+// entries: per row, the larger of `floor_per_row` and 1.25 x the largest ratio
+// seen on this device, so a stream of similar patterns stops overflowing (an
+// overflow reruns the traversal).
+long long pool_estimate(Ctx* c, long long rows, long long floor_per_row, long long full) {
+  double per_row;
+  {
+    std::lock_guard<std::mutex> lk(c->hmu);
+    per_row = 1.25 * c->rows_ratio;
+  }
+  if (per_row < (double)floor_per_row) per_row = (double)floor_per_row;
+  long long cap = (long long)(per_row * (double)rows) + (1 << 20);
+  if (full > 0 && cap > full) cap = full;
+  if (cap < 1024) cap = 1024;
+  return cap;
+}
+
+void note_pool_use(Ctx* c, unsigned long long used, long long rows) {
+  if (rows <= 0) return;
+  const double r = (double)used / (double)rows;
+  std::lock_guard<std::mutex> lk(c->hmu);
+  if (r > c->rows_ratio) c->rows_ratio = r;
 }
 
 // Bytes of one global-tier slot of capacity cap (a multiple of 1024 vertices).
@@ -469,11 +494,9 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   {
     std::lock_guard<std::mutex> lk(c->hmu);
     auto it = c->pool_hint.find(n);
-    pool_cap = it != c->pool_hint.end() ? it->second : (long long)256 * n + (1 << 20);
-    const long long full = (long long)n * (long long)(n + 1);
-    if (pool_cap > full) pool_cap = full;
-    if (pool_cap < 1024) pool_cap = 1024;
+    if (it != c->pool_hint.end()) pool_cap = it->second;
   }
+  if (pool_cap == 0) pool_cap = pool_estimate(c, n, 256, (long long)n * (long long)(n + 1));
   CK(palloc(c, &pool, (size_t)pool_cap, st));
   if (plan.S > 0) {
     spill_cap = plan.S > plan.list_cap ? plan.S - plan.list_cap : 1;
@@ -575,6 +598,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     std::lock_guard<std::mutex> lk(c->hmu);
     c->pool_hint[n] = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
   }
+  note_pool_use(c, h->pool_cursor, n);
 
   out->nnz_L = (int64_t)h->total_L;
   out->nnz_U = (int64_t)h->total_U;
@@ -1052,8 +1076,9 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
   {
     std::lock_guard<std::mutex> lk(c->hmu);
     auto it = c->pool_hint.find(-(int32_t)(sig & 0x7FFFFFFF) - 1);
-    p->pool_cap = it != c->pool_hint.end() ? it->second : 64 * p->N + (1 << 20);
+    p->pool_cap = it != c->pool_hint.end() ? it->second : 0;
   }
+  if (p->pool_cap == 0) p->pool_cap = pool_estimate(c, p->N, 64, 0);
   if (transient) {
     const size_t b_mats = sizeof(MatDesc) * (size_t)(p->B > 0 ? p->B : 1);
     const size_t b_is = sizeof(int32_t) * item_start.size();
@@ -1182,6 +1207,7 @@ int batch_phase1(Ctx* c, BatchPlan* p, const gsofa_options& o, cudaStream_t st, 
     const DevCounters* h = p->hctr();
     if (h->err & ERR_INPUT) return GSOFA_E_INVAL;
     if (h->err & ERR_NOCONV) return GSOFA_E_NOCONVERGE;
+    note_pool_use(c, h->pool_cursor, p->N);
     if (!(h->err & ERR_OVERFLOW)) return GSOFA_OK;
     // the row pool was too small; the totals are exact now
     const long long need = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
