@@ -67,52 +67,99 @@ def _stats(res: gsofa_result) -> dict:
     return {f: getattr(s, f) for f, _ in s._fields_}
 
 
+_FIELDS = ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start")
+
+
 class DeviceResult:
-    """Device-resident result; the tensors alias library memory (freed when all are gone)."""
+    """Device-resident result; the arrays alias library memory (freed when the
+    result and every tensor taken from it are gone).  Tensors are created on
+    first access."""
 
     def __init__(self, res: gsofa_result, stream: int):
-        import torch
-        own = _Owner(res)
-        n = res.n
-
-        def t(ptr, count, typestr, dtype):
-            if count == 0:
-                return torch.empty(0, dtype=dtype, device="cuda")
-            return torch.as_tensor(_CAI(ptr, count, typestr, own, stream), device="cuda")
-
-        self.n = n
+        self._owner = _Owner(res)
+        self._stream = stream
+        self._t = {}
+        self.n = res.n
         self.nnz_L = int(res.nnz_L)
         self.nnz_U = int(res.nnz_U)
         self.n_super = int(res.n_super)
-        self.L_rowptr = t(res.L_rowptr, n + 1, "<i8", torch.int64)
-        self.L_colidx = t(res.L_colidx, res.nnz_L, "<i4", torch.int32)
-        self.U_rowptr = t(res.U_rowptr, n + 1, "<i8", torch.int64)
-        self.U_colidx = t(res.U_colidx, res.nnz_U, "<i4", torch.int32)
-        self.fill_count = t(res.fill_count, n, "<i4", torch.int32)
-        self.super_start = t(res.super_start, res.n_super + 1, "<i4", torch.int32)
         self.stats = _stats(res)
-        self._owner = own
+
+    def _raw(self, name: str):
+        """(device pointer, element count, typestr, torch dtype) of one output array."""
+        import torch
+        r, n = self._owner.res, self.n
+        return {"L_rowptr": (r.L_rowptr, n + 1, "<i8", torch.int64),
+                "L_colidx": (r.L_colidx, self.nnz_L, "<i4", torch.int32),
+                "U_rowptr": (r.U_rowptr, n + 1, "<i8", torch.int64),
+                "U_colidx": (r.U_colidx, self.nnz_U, "<i4", torch.int32),
+                "fill_count": (r.fill_count, n, "<i4", torch.int32),
+                "super_start": (r.super_start, self.n_super + 1, "<i4", torch.int32)}[name]
+
+    def _tensor(self, name: str):
+        import torch
+        t = self._t.get(name)
+        if t is None:
+            ptr, count, typestr, dtype = self._raw(name)
+            if count == 0:
+                t = torch.empty(0, dtype=dtype, device="cuda")
+            else:
+                t = torch.as_tensor(_CAI(ptr, count, typestr, self._owner, self._stream), device="cuda")
+            self._t[name] = t
+        return t
+
+    L_rowptr = property(lambda self: self._tensor("L_rowptr"))
+    L_colidx = property(lambda self: self._tensor("L_colidx"))
+    U_rowptr = property(lambda self: self._tensor("U_rowptr"))
+    U_colidx = property(lambda self: self._tensor("U_colidx"))
+    fill_count = property(lambda self: self._tensor("fill_count"))
+    super_start = property(lambda self: self._tensor("super_start"))
 
     def to_host(self) -> "HostResult":
         return results_to_host([self])[0]
 
 
 def results_to_host(results) -> list:
-    """Copy device results to host arrays: one asynchronous copy per array into
-    pinned memory on the current stream, then one synchronisation for all."""
+    """Copy device results to host arrays through pinned memory on the current
+    stream, with one synchronisation for all.  Arrays that are adjacent in device
+    memory (the results of one batch share one block per field) are copied as
+    one span, so a batch costs a few large copies instead of six per matrix."""
     import torch
-    names = ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start")
-    staged = []
-    for r in results:
-        hs = []
-        for nm in names:
-            a = getattr(r, nm)
-            h = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
-            h.copy_(a, non_blocking=True)
-            hs.append(h)
-        staged.append(hs)
+    out = [[None] * len(_FIELDS) for _ in results]
+    pending = []
+    for f, nm in enumerate(_FIELDS):
+        arrs = []
+        for k, r in enumerate(results):
+            ptr, count, typestr, dtype = r._raw(nm)
+            if count == 0:
+                out[k][f] = (torch.empty(0, dtype=dtype), 0, 0)
+            else:
+                arrs.append((int(ptr), int(count), typestr, dtype, k))
+        arrs.sort(key=lambda x: x[0])
+        i = 0
+        while i < len(arrs):
+            ptr0, _, typestr, dtype, _ = arrs[i]
+            esz = 8 if typestr == "<i8" else 4
+            end = ptr0 + arrs[i][1] * esz
+            j = i + 1
+            while j < len(arrs) and arrs[j][2] == typestr and arrs[j][0] == end:
+                end += arrs[j][1] * esz
+                j += 1
+            group = arrs[i:j]
+            total = sum(g[1] for g in group)
+            owners = [results[g[4]]._owner for g in group]
+            span = torch.as_tensor(_CAI(ptr0, total, typestr, owners, results[group[0][4]]._stream),
+                                   device="cuda")
+            h = torch.empty(total, dtype=dtype, pin_memory=True)
+            h.copy_(span, non_blocking=True)
+            pending.append((span, h))
+            off = 0
+            for g in group:
+                out[g[4]][f] = (h, off, g[1])
+                off += g[1]
+            i = j
     torch.cuda.current_stream().synchronize()
-    return [HostResult(r.n, *[h.numpy() for h in hs], r.stats) for r, hs in zip(results, staged)]
+    return [HostResult(r.n, *[h[o:o + c].numpy() for h, o, c in out[k]], r.stats) for k, r in enumerate(results)]
 
 
 class HostResult:

@@ -72,10 +72,11 @@ def test_batch_replay_autotune_and_alone_equal():
     r8 = [r.to_host() for r in gs.batch_device(dev, opts=gs.options(frontier_order=1, expand_mode=3,
                                                                       list_capacity=64))]
     r9 = [r.to_host() for r in gs.batch_device(dev, opts=gs.options(frontier_order=1, expand_mode=2))]
+    r10 = gs.results_to_host(gs.batch_device(dev))  # adjacent arrays copied as spans
     torch.cuda.synchronize()
     for k, (A, (rp, ci)) in enumerate(zip(mats, dev)):
         alone = gs.symbolic_device(rp, ci).to_host()
-        for r in (r1[k], r2[k], r3[k], r4[k], r5[k], r6[k], r7[k], r8[k], r9[k]):
+        for r in (r1[k], r2[k], r3[k], r4[k], r5[k], r6[k], r7[k], r8[k], r9[k], r10[k]):
             for key in ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start"):
                 assert np.array_equal(getattr(r, key), getattr(alone, key)), (k, key)
         assert_same(alone, oracle_full(A))
