@@ -77,7 +77,11 @@ typedef struct gsofa_options {
                                     2 CSR edge-balanced (a warp flattens its rows' entries), 3 16-byte
                                     records of 16-bit column offsets built from the CSR (rows that do
                                     not fit fall back to the CSR) */
-    int32_t reserved[3];
+    int32_t schedule;            /* shared-memory tier: 0 automatic, 1 breadth-first levels with one
+                                    barrier each, 2 a worklist without level barriers (warps take
+                                    queued vertices as they come; 16-bit labels and every vertex on
+                                    chip only, else levels).  Same result */
+    int32_t reserved[2];
 } gsofa_options;
 
 /* Per-call statistics (filled when options.collect_stats == 1). */

@@ -37,7 +37,8 @@ class gsofa_options(ctypes.Structure):
         ("frontier_order", ctypes.c_int32),
         ("label_bits", ctypes.c_int32),
         ("expand_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("schedule", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

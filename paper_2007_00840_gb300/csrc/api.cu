@@ -316,6 +316,7 @@ struct Plan {
   int smem_grid = 0;
   int glob_block = 512;
   int glob_grid = 0;
+  int async_sched = 0;    // shared tier: worklist schedule (the two lists form one ring >= S)
 };
 
 }  // namespace
@@ -385,6 +386,19 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     p->list_cap = cap;
     p->smem_block = block;
     p->smem_grid = c->sms * occ;
+    if (o.schedule == 2 && label16 && S >= n && (o.expand_mode == 0 || o.expand_mode == 3) && !o.fill_first) {
+      // worklist schedule: a ring of 2 x cap >= S entries, as many threads as fit
+      const int32_t rcap = (S + 1) / 2 > 32 ? (S + 1) / 2 : 32;
+      const size_t bytes = trav_smem_bytes(n, S, rcap, 1);
+      const int tb = o.threads_per_source > 0 ? o.threads_per_source : 1024;
+      const int aocc = bytes <= limit ? trav_smem_occupancy(tb, bytes, 1) : 0;
+      if (aocc > 0) {
+        p->async_sched = 1;
+        p->list_cap = rcap;
+        p->smem_block = tb;
+        p->smem_grid = c->sms * aocc;
+      }
+    }
     if (o.max_ctas > 0 && o.max_ctas < p->smem_grid) p->smem_grid = o.max_ctas;
   }
   if (S < n) {
@@ -420,6 +434,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->label_bits = in->label_bits;
   if (in->expand_mode < 0 || in->expand_mode > 3) return GSOFA_E_INVAL;
   o->expand_mode = in->expand_mode;
+  if (in->schedule < 0 || in->schedule > 2) return GSOFA_E_INVAL;
+  o->schedule = in->schedule;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -570,6 +586,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.spill_cap = spill_cap;
       a.chunk = o.work_chunk > 0 ? o.work_chunk : 1;
       a.expand_mode = o.expand_mode == 0 ? 3 : o.expand_mode;
+      a.async_sched = plan.async_sched;
       a.ell = ell;
       LK(launch_trav_smem(a, plan.smem_grid, plan.smem_block, plan.label16, st));
     }

@@ -101,6 +101,7 @@ struct TravArgs {
   uint32_t* g_base;                   // per slot: current maxId window base (persists across launches)
   int64_t g_cap;                      // per-slot capacity in vertices (>= n, multiple of 1024)
   int32_t g_slots;                    // number of slots (warps) of the launch
+  int32_t async_sched;                // shared-memory tier: worklist without level barriers (16-bit, S >= n)
 };
 
 // ---- launchers (return cudaGetLastError())

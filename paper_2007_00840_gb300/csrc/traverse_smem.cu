@@ -282,11 +282,179 @@ size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
   return label16 ? trav_smem_bytes_t<uint16_t>(n, S, cap) : trav_smem_bytes_t<uint32_t>(n, S, cap);
 }
 
+constexpr uint16_t RING_EMPTY = 0xFFFFu;  // vertex ids of the 16-bit tier are <= 65532
+constexpr long long ASYNC_WAIT_CYCLES = 2000000000LL;  // bound of every wait (about 1 s)
+
+// A wait gives up when its bound passes or another wait already gave up.
+__device__ __forceinline__ bool wait_expired(long long t0, DevCounters* ctr) {
+  if (*(volatile int32_t*)&ctr->err & ERR_NOCONV) return true;
+  if (clock64() - t0 > ASYNC_WAIT_CYCLES) {
+    atomicOr(&ctr->err, ERR_NOCONV);
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_sc_cta() { asm volatile("fence.sc.cta;" ::: "memory"); }
+
+// relax_ul for the asynchronous schedule: the in-queue bit is examined by an
+// atomic after a sequentially consistent fence, so that either this lane sees
+// a popper's clearing of the bit (and queues w again) or the popper, which
+// fences between clearing the bit and reading the label, sees the new label.
+__device__ __forceinline__ int relax_async(const Src<uint16_t>& c, int w, uint32_t nmE) {
+  const uint32_t wE = c.base + 1u + (uint32_t)w;
+  uint32_t old;
+  if (!LabOps<uint16_t>::lower(c.lab, w, nmE, &old) || w >= c.s || old <= wE) return 0;
+  fence_sc_cta();
+  const uint32_t bit = 1u << (w & 31);
+  return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
+}
+
+// Ring slot of position p (positions grow without bound within a source).
+__device__ __forceinline__ int ring_slot(int p, int qs) { return p % qs; }
+
+// Push `cnt` vertices of this lane (in w[0..7] where bit q of em is set) to
+// the ring; all 32 lanes call this.  pending is raised before the positions
+// are taken, so a warp that sees pending == 0 knows nothing is queued or being
+// processed.  A slot from the previous lap may still be in a popper's hands
+// (reserved, not yet read): wait for it, bounded.
+__device__ __forceinline__ void ring_push8(uint16_t* ring, int qs, int* head_tail_pend, const int (&wv)[8],
+                                           unsigned em, int lane, DevCounters* ctr) {
+  const int cnt = __popc(em);
+  const int incl = warp_incl_scan(cnt, lane);
+  const int tot = __shfl_sync(FULL, incl, 31);
+  if (!tot) return;
+  int basep = 0;
+  if (lane == 31) {
+    atomicAdd(&head_tail_pend[2], tot);
+    basep = atomicAdd(&head_tail_pend[1], tot);
+  }
+  basep = __shfl_sync(FULL, basep, 31);
+  int pos = basep + incl - cnt;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    if ((em >> q) & 1u) {
+      volatile uint16_t* sl = ring + ring_slot(pos, qs);
+      const long long t0 = clock64();
+      while (*sl != RING_EMPTY)
+        if (wait_expired(t0, ctr)) break;
+      *sl = (uint16_t)wv[q];
+      pos++;
+    }
+  }
+}
+
+// The asynchronous schedule of one source (16-bit labels, every vertex with a
+// label slot, ELL records): instead of breadth-first levels separated by
+// barriers, warps take up to 32 queued vertices at a time from a ring in
+// shared memory and queue what they lower.  Dn is the in-queue bitmap (one bit
+// per vertex: queued and not yet taken), so the ring never holds more than S
+// entries.  Ends when nothing is queued and no warp holds taken work.
+__device__ void async_source(const Src<uint16_t>& c, const TravArgs& a, uint16_t* ring, int qs, int* htp,
+                             long long rowb, uint32_t base, const int32_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ colidx, int lane, unsigned long long& n_exp,
+                             unsigned long long& n_edge, int* bad) {
+  const unsigned lt = (1u << lane) - 1u;
+  long long idle0 = -1;
+  for (;;) {
+    int h = 0, take = 0;
+    if (lane == 0) {
+      int hh = *(volatile int*)&htp[0];
+      for (;;) {
+        const int avail = *(volatile int*)&htp[1] - hh;
+        take = avail < 32 ? avail : 32;
+        if (take <= 0) break;
+        const int prev = atomicCAS(&htp[0], hh, hh + take);
+        if (prev == hh) break;
+        hh = prev;
+      }
+      h = hh;
+      if (take <= 0) {
+        if (*(volatile int*)&htp[2] == 0) {
+          take = -1;  // finished
+        } else {
+          if (idle0 < 0) idle0 = clock64();
+          else if (wait_expired(idle0, a.ctr)) take = -1;
+        }
+      } else {
+        idle0 = -1;
+      }
+    }
+    take = __shfl_sync(FULL, take, 0);
+    if (take < 0) break;
+    if (take == 0) {
+      __nanosleep(64);
+      continue;
+    }
+    h = __shfl_sync(FULL, h, 0);
+    int v = -1;
+    uint32_t nmE = 0u;
+    if (lane < take) {
+      volatile uint16_t* sl = ring + ring_slot(h + lane, qs);
+      uint16_t x;
+      const long long t0 = clock64();
+      while ((x = *sl) == RING_EMPTY)
+        if (wait_expired(t0, a.ctr)) break;
+      *sl = RING_EMPTY;
+      v = x == RING_EMPTY ? -1 : (int)x;
+      if (v >= 0) {
+        atomicAnd(&c.Dn[v >> 5], ~(1u << (v & 31)));  // v leaves the queue before its label is read
+        fence_sc_cta();
+        const uint32_t lv = (uint32_t)((volatile uint16_t*)c.lab)[v];
+        const uint32_t vE = base + 1u + (uint32_t)v;
+        nmE = lv > vE ? lv : vE;
+        n_exp++;
+        if (a.collect_stats) n_edge += (unsigned long long)(__ldg(rowptr + v + 1) - __ldg(rowptr + v));
+      }
+    }
+    bool fb = false;
+    uint32_t h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
+    if (v >= 0) {
+      const int4 r4 = __ldg(a.ell + rowb + v);
+      h0 = (uint32_t)r4.x; h1 = (uint32_t)r4.y; h2 = (uint32_t)r4.z; h3 = (uint32_t)r4.w;
+      fb = (h0 & 0xFFFFu) == 0x8000u;
+      if (fb) h0 = 0u;
+    }
+    int wv[8];
+    wv[0] = v + (int)(short)(h0 & 0xFFFFu); wv[1] = v + (int)(short)(h0 >> 16);
+    wv[2] = v + (int)(short)(h1 & 0xFFFFu); wv[3] = v + (int)(short)(h1 >> 16);
+    wv[4] = v + (int)(short)(h2 & 0xFFFFu); wv[5] = v + (int)(short)(h2 >> 16);
+    wv[6] = v + (int)(short)(h3 & 0xFFFFu); wv[7] = v + (int)(short)(h3 >> 16);
+    unsigned em = 0u;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (wv[q] != v && relax_async(c, wv[q], nmE)) em |= 1u << q;
+    ring_push8(ring, qs, htp, wv, em, lane, a.ctr);
+    // rows without a record: the whole warp walks each from the CSR
+    unsigned fm = __ballot_sync(FULL, fb);
+    while (fm) {
+      const int l = __ffs(fm) - 1;
+      fm &= fm - 1u;
+      const int u = __shfl_sync(FULL, v, l);
+      const uint32_t unm = __shfl_sync(FULL, nmE, l);
+      const int eb = __ldg(rowptr + u), ee = __ldg(rowptr + u + 1);
+      for (int e0 = eb; e0 < ee; e0 += 32) {
+        const int e = e0 + lane;
+        int w[8] = {u, u, u, u, u, u, u, u};
+        unsigned en = 0u;
+        if (e < ee) {
+          w[0] = __ldg(colidx + e);
+          if ((unsigned)w[0] >= (unsigned)c.n) { *bad = 1; w[0] = u; }
+          if (w[0] != u && relax_async(c, w[0], unm)) en = 1u;
+        }
+        ring_push8(ring, qs, htp, w, en, lane, a.ctr);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) atomicSub(&htp[2], take);  // the taken entries are done (their pushes are in)
+  }
+}
+
 // EB: edge-balanced expansion (the warp flattens the rows of its 32 frontier
 // vertices so every lane works on an entry) instead of lock-step row slots.
 // FF: the optional fill-first check of Section 4.
 // ELL: read rows from the 16-bit offset records (CSR only for rows that do not fit).
-template <typename LabT, bool EB, bool FF, bool ELL, bool UL>
+template <typename LabT, bool EB, bool FF, bool ELL, bool UL, bool ASYNC>
 __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n_max = a.n, S = a.S, CAP = a.list_cap;
@@ -317,6 +485,10 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   for (int i = tid; i < S; i += nthr) lab[i] = (LabT)LabOps<LabT>::MAXV;
   for (int i = tid; i < SW; i += nthr) { D0[i] = 0u; D1[i] = 0u; }
   for (int i = tid; i < NWmax; i += nthr) ub[i] = 0u;
+  // asynchronous schedule: the two lists form one ring of 2 x CAP >= S entries
+  const int QS = 2 * CAP;
+  if (ASYNC)
+    for (int i = tid; i < QS; i += nthr) L0[i] = (LabT)RING_EMPTY;
 
   // window base of the previous source; MAXV stands for the fill value
   uint32_t base = LabOps<LabT>::MAXV;
@@ -393,8 +565,13 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         lab[w] = (LabT)base;  // encoded -1
         const uint32_t bit = 1u << (w & 31);
         if (!(atomicOr(&D0[w >> 5], bit) & bit)) {  // once per vertex: the list holds < s entries
-          const int pos = atomicAdd(&s_q[0], 1);
-          if (pos < CAP) L0[pos] = (LabT)w; else S0[pos - CAP] = w;
+          if (ASYNC) {  // queue it: s_q = {head, tail, pending}
+            atomicAdd(&s_q[2], 1);
+            L0[atomicAdd(&s_q[1], 1)] = (LabT)w;  // the ring is empty and deg(s) < QS
+          } else {
+            const int pos = atomicAdd(&s_q[0], 1);
+            if (pos < CAP) L0[pos] = (LabT)w; else S0[pos - CAP] = w;
+          }
         }
       } else if (w > s) {
         if (UL) lab[w] = (LabT)base;  // any value of the window marks a U entry
@@ -409,10 +586,17 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     // hops (each changed vertex is expanded again); simple paths through
     // vertices below s have at most s hops, so level s+2 changes nothing.
     const int cap_lv = s + 3;
-    int qc = s_q[0];
+    int qc = ASYNC ? 0 : s_q[0];
     long long t_start = 0;
     if (a.collect_stats && tid == 0) t_start = clock64();
     int L = 1;
+    if constexpr (ASYNC) {
+      if constexpr (sizeof(LabT) == 2) {
+        Src<uint16_t> c{lab, ub, D0, L0, S0, &s_q[1], base, s, n, CAP};
+        async_source(c, a, (uint16_t*)L0, QS, s_q, rowb, base, rowptr, colidx, lane, n_exp, n_edge, &bad);
+      }
+      __syncthreads();
+    }
     for (; qc > 0; L++) {
       const int cb = (L - 1) & 1, nb = L & 1;
       LabT* Lc = cb ? L1 : L0;
@@ -744,12 +928,12 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16) {
   return label16 ? max_S_t<uint16_t>(n, smem_limit, 1024) : max_S_t<uint32_t>(n, smem_limit, 1024);
 }
 
-template <typename LabT, bool EB, bool FF, bool ELL, bool UL>
+template <typename LabT, bool EB, bool FF, bool ELL, bool UL, bool ASYNC = false>
 static cudaError_t launch_t(const TravArgs& a, int grid, int block, size_t bytes, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<LabT, EB, FF, ELL, UL>,
+  cudaError_t e = cudaFuncSetAttribute(trav_smem_kernel<LabT, EB, FF, ELL, UL, ASYNC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  trav_smem_kernel<LabT, EB, FF, ELL, UL><<<grid, block, bytes, st>>>(a);
+  trav_smem_kernel<LabT, EB, FF, ELL, UL, ASYNC><<<grid, block, bytes, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -758,8 +942,15 @@ static cudaError_t launch_l(const TravArgs& a, int grid, int block, size_t bytes
   const bool ff = a.fill_first != 0;
   if (a.ell) {
     // U entries by labels when every vertex has a label slot
-    if (a.S >= a.n) return ff ? launch_t<LabT, false, true, true, true>(a, grid, block, bytes, st)
-                              : launch_t<LabT, false, false, true, true>(a, grid, block, bytes, st);
+    if (a.S >= a.n) {
+      if constexpr (sizeof(LabT) == 2) {
+        // asynchronous schedule (the ring of 2 x list_cap entries must hold S)
+        if (a.async_sched && !ff && 2 * a.list_cap >= a.S && 2 * a.list_cap >= 64)
+          return launch_t<LabT, false, false, true, true, true>(a, grid, block, bytes, st);
+      }
+      return ff ? launch_t<LabT, false, true, true, true>(a, grid, block, bytes, st)
+                : launch_t<LabT, false, false, true, true>(a, grid, block, bytes, st);
+    }
     return ff ? launch_t<LabT, false, true, true, false>(a, grid, block, bytes, st)
               : launch_t<LabT, false, false, true, false>(a, grid, block, bytes, st);
   }
@@ -776,7 +967,7 @@ cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16
 
 int trav_smem_static_bytes() {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t, false, false, false, false>) != cudaSuccess) {
+  if (cudaFuncGetAttributes(&fa, trav_smem_kernel<uint32_t, false, false, false, false, false>) != cudaSuccess) {
     cudaGetLastError();
     return 1024;
   }
@@ -784,8 +975,8 @@ int trav_smem_static_bytes() {
 }
 
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16) {
-  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t, false, false, true, true>
-                          : (const void*)trav_smem_kernel<uint32_t, false, false, true, true>;
+  const void* f = label16 ? (const void*)trav_smem_kernel<uint16_t, false, false, true, true, false>
+                          : (const void*)trav_smem_kernel<uint32_t, false, false, true, true, false>;
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -87,6 +87,25 @@ def test_frontier_orders_and_autotune():
             assert_same(run_gpu(A, **opt), o), (A.name, opt)
 
 
+def test_worklist_schedule_exact():
+    """The shared-memory tier without level barriers (schedule = 2) gives the same rows."""
+    rng = np.random.default_rng(5)
+    rr, cc = [], []
+    for i in range(400):  # a few rows with more than 8 neighbours (read from the CSR)
+        k = 40 if i % 53 == 0 else 3
+        cols = rng.choice(400, size=k, replace=False)
+        rr += [i] * k
+        cc += cols.tolist()
+    cases = [synth.config(0), synth.grid2d(40, 0.7, seed=21), synth.banded(2500, 30, seed=22),
+             synth.random_pattern(300, 0.02, seed=24, diag=False), synth.random_pattern(20, 0.3, seed=5),
+             synth._csr_from_pairs(400, np.array(rr), np.array(cc), "bigdeg"), load_paper_example()[0]]
+    for A in cases:
+        assert_same(run_gpu(A, schedule=2), oracle_full(A)), A.name
+        assert_same(run_gpu(A, schedule=2, threads_per_source=256), oracle_full(A)), A.name
+    A = synth.config(1)
+    assert_same(run_gpu(A, schedule=2), oracle_full(A, nthreads=16))
+
+
 def test_empty_matrix():
     A = synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), "empty")
     h = run_gpu(A)
