@@ -573,7 +573,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
         a.g_slots = plan.glob_grid;
       }
       LK(launch_trav_global(a, (plan.glob_grid + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
-                            plan.glob_block, st));
+                            plan.glob_block, st, 32));
       CK(cudaEventRecord(c->g_done, st));
     }
     ev.rec(3, st);
@@ -876,9 +876,10 @@ std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, si
       }
     }
   }
-  for (int per_sm : (order == 1 ? std::vector<int>{} : std::vector<int>{16, 32})) {
+  for (int per_sm : (order == 1 ? std::vector<int>{} : std::vector<int>{16, 32, 40})) {
     LaunchShape sh;
     sh.kernel = 1;
+    sh.occ = per_sm;  // warps per SM (above 32: the 48-register build)
     sh.slots = class_slots(c, n_max, per_sm);
     if (sh.slots > 0) out.push_back(sh);
   }
@@ -939,7 +940,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
     a.g_cap = p.c_cap;
     a.g_slots = p.shape.slots;
     if ((e = launch_trav_global(a, (p.shape.slots + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
-                                32 * GLOBAL_WARPS_PER_CTA, st)) != cudaSuccess)
+                                32 * GLOBAL_WARPS_PER_CTA, st, p.shape.occ)) != cudaSuccess)
       return e;
   } else if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) {
     return e;
@@ -1346,10 +1347,11 @@ LaunchShape default_shape(Ctx* c, BatchCache& bc, const BatchPlan* p, const gsof
   auto tt = bc.tuned.find(key);
   if (tt != bc.tuned.end() && o.list_capacity == 0 && o.work_chunk == 0) return tt->second;
   if (o.threads_per_source == 0 && o.list_capacity == 0 && o.work_chunk == 0 && o.frontier_order != 1) {
-    // untuned default: the class-ordered warp tier (fewest expansions)
+    // untuned default: the class-ordered warp tier (fewest expansions), 40 warps per SM
     sh.kernel = 1;
-    sh.slots = class_slots(c, p->n_max, 32);
-    if (o.max_ctas > 0 && sh.slots > o.max_ctas * 16) sh.slots = o.max_ctas * 16;
+    sh.occ = 40;
+    sh.slots = class_slots(c, p->n_max, 40);
+    if (o.max_ctas > 0 && sh.slots > o.max_ctas * GLOBAL_WARPS_PER_CTA) sh.slots = o.max_ctas * GLOBAL_WARPS_PER_CTA;
     if (sh.slots > 0) { *rc = GSOFA_OK; return sh; }
     sh.kernel = 0;
   }

@@ -110,7 +110,9 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16);
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st);
 int trav_smem_static_bytes();
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16);
-cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st);
+// warps_per_sm: the slots per SM the launch was sized for (above 32: the
+// 48-register build of the kernel)
+cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st, int warps_per_sm);
 
 cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,
                             DevCounters* ctr, cudaStream_t st);

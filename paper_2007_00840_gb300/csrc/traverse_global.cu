@@ -117,34 +117,50 @@ __device__ __forceinline__ int relax_class(const Slot& sl, int w, int s, int t, 
   return 0;
 }
 
-// Relax the (up to 8) neighbours of one vertex read from its ELL record for
+// Relax neighbours Q0 .. Q0+K-1 of one vertex read from its ELL record for
 // class t: w = v + offset, in [0, n) by construction of the records, empty
 // slots hold w == v.  The label updates are issued together; vertices above s
 // are U entries, lowered vertices above t are pending fills (their own class
 // later).  Returns the slots whose vertex joins class t.
-__device__ __forceinline__ unsigned relax8_class(const Slot& sl, const int (&wv)[8], int v, int s, int t,
-                                                 uint32_t pE) {
-  uint32_t old[8];
+template <int Q0, int K>
+__device__ __forceinline__ unsigned relax_slots_class(const Slot& sl, const int (&wv)[8], int v, int s, int t,
+                                                      uint32_t pE) {
+  uint32_t old[K];
 #pragma unroll
-  for (int q = 0; q < 8; q++) old[q] = gmin_if(&sl.lab[wv[q] < 0 ? 0 : wv[q]], pE, wv[q] != v && wv[q] < s);
+  for (int q = 0; q < K; q++)
+    old[q] = gmin_if(&sl.lab[wv[Q0 + q] < 0 ? 0 : wv[Q0 + q]], pE, wv[Q0 + q] != v && wv[Q0 + q] < s);
   unsigned em = 0u;
 #pragma unroll
-  for (int q = 0; q < 8; q++) {
-    const int w = wv[q];
+  for (int q = 0; q < K; q++) {
+    const int w = wv[Q0 + q];
     if (w == v) continue;
     if (w > s) {
       red_bit2(sl.U, sl.US, w);
     } else if (w < s && old[q] > pE) {  // first reached, now with maxId t
-      if (w < t) em |= 1u << q;          // same class
+      if (w < t) em |= 1u << (Q0 + q);   // same class
       else red_bit2(sl.P, sl.PS, w);     // a fill of L(s,:)
     }
   }
   return em;
 }
 
+// All 8 slots in one group, or (when registers are scarce, MINB > 8) in two
+// groups of 4.
+template <int MINB>
+__device__ __forceinline__ unsigned relax8_class(const Slot& sl, const int (&wv)[8], int v, int s, int t,
+                                                 uint32_t pE) {
+  if constexpr (MINB > 8)
+    return relax_slots_class<0, 4>(sl, wv, v, s, t, pE) | relax_slots_class<4, 4>(sl, wv, v, s, t, pE);
+  else
+    return relax_slots_class<0, 8>(sl, wv, v, s, t, pE);
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
+// MINB: CTAs of 4 warps per SM the register budget is sized for (8: 32 warps
+// per SM with up to 64 registers; 10: 40 warps with up to 48).
+template <int MINB>
+__global__ void __launch_bounds__(32 * GLOBAL_WARPS_PER_CTA, MINB) trav_global_kernel(TravArgs a) {
   const int lane = threadIdx.x & 31;
   const int slot = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (slot >= a.g_slots) return;
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
             wv[2] = v + (int)(short)(h1 & 0xFFFFu); wv[3] = v + (int)(short)(h1 >> 16);
             wv[4] = v + (int)(short)(h2 & 0xFFFFu); wv[5] = v + (int)(short)(h2 >> 16);
             wv[6] = v + (int)(short)(h3 & 0xFFFFu); wv[7] = v + (int)(short)(h3 >> 16);
-            const unsigned em = v >= 0 ? relax8_class(sl, wv, v, s, t, pE) : 0u;
+            const unsigned em = v >= 0 ? relax8_class<MINB>(sl, wv, v, s, t, pE) : 0u;
             const int cnt = __popc(em);
             int inc = cnt;
 #pragma unroll
@@ -447,8 +463,10 @@ __global__ void __launch_bounds__(512) trav_global_kernel(TravArgs a) {
   }
 }
 
-cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st) {
-  trav_global_kernel<<<grid, block, 0, st>>>(a);
+cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st, int warps_per_sm) {
+  if (block != 32 * GLOBAL_WARPS_PER_CTA) return cudaErrorInvalidConfiguration;
+  if (warps_per_sm > 32) trav_global_kernel<10><<<grid, block, 0, st>>>(a);
+  else trav_global_kernel<8><<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 
