@@ -104,8 +104,9 @@ __device__ __forceinline__ int relax_low(const Src<LabT>& c, int w, uint32_t nmE
   if (FF && (uint32_t)c.lab[w] < wE) return 0;
   uint32_t old;
   if (!LabOps<LabT>::lower(c.lab, w, nmE, &old) || old <= wE) return 0;
+  // nearly every lowering that reaches here is a vertex's first entry into the
+  // list, so a read of the bit before the atomic would rarely save it
   const uint32_t bit = 1u << (w & 31);
-  if (c.Dn[w >> 5] & bit) return 0;
   return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
 }
 
@@ -120,8 +121,9 @@ __device__ __forceinline__ int relax_ul(const Src<LabT>& c, int w, uint32_t nmE)
   if (FF && w < c.s && (uint32_t)c.lab[w] < wE) return 0;
   uint32_t old;
   if (!LabOps<LabT>::lower(c.lab, w, nmE, &old) || w >= c.s || old <= wE) return 0;
+  // nearly every lowering that reaches here is a vertex's first entry into the
+  // list, so a read of the bit before the atomic would rarely save it
   const uint32_t bit = 1u << (w & 31);
-  if (c.Dn[w >> 5] & bit) return 0;
   return (atomicOr(&c.Dn[w >> 5], bit) & bit) ? 0 : 1;
 }
 
