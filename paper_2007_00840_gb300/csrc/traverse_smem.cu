@@ -4,18 +4,19 @@
 // work counter (persistent CTAs, largest source first).  Per source it keeps
 // in shared memory:
 //   lab[0..S)   maxId of every vertex below the source (bubble removal,
-//               Section 6: vertices above s never need one).  16-bit when the
-//               matrix order allows it, else 32-bit.  Values use the
-//               value-range windows of Section 4 ("Optimizing the
-//               initialization of maxId"): the k-th source of this CTA uses the
-//               window [base_k, base_k + s_k] with base_k decreasing, so any
-//               value above the window reads as "not reached" and lab[] is
-//               refilled only when the range is used up;
+//               Section 6: vertices above s never need one), or of every
+//               vertex of the matrix when S >= n (then also used for U, see
+//               below).  16-bit when the matrix order allows it, else 32-bit.
+//               Values use the value-range windows of Section 4 ("Optimizing
+//               the initialization of maxId"): the k-th source of this CTA
+//               uses the window [base_k, base_k + s_k] with base_k decreasing,
+//               so any value above the window reads as "not reached" and lab[]
+//               is refilled only when the range is used up;
 //   list0/list1 the current and next frontier as compact lists; entries past
 //               the list capacity spill to a per-CTA area in global memory (the
 //               external frontier management of Section 6, one level down);
 //   D0/D1       dedup bitmaps: bit v of D[b] is set iff v is in list b;
-//   ub          the U part of the row as a bitmap over [0, n).
+//   ub          the U part of the row as a bitmap over [0, n) (when S < n).
 // maxId of a vertex is the smallest "largest intermediate vertex" over the
 // paths found so far; a direct neighbour of s has no intermediate (-1).
 //
@@ -23,11 +24,14 @@
 // neighbour w (atomic min).  If the proposal lowers maxId(w) and w was not
 // already a fill (old > w), w's own proposal changed, so w joins the next
 // frontier; w is a fill of L(s,:) iff its final maxId < w (Theorem 1).
-// Neighbours above s are U entries.  Lanes of a warp take consecutive list
-// entries; a warp walks the adjacency rows of its 32 vertices in lock-step,
-// issuing a batch of independent column loads per step, and appends newly
-// queued vertices with one shared-memory atomic per warp.  One barrier per
-// level.
+// Neighbours above s are U entries: with a label slot for every vertex they
+// are recorded by lowering their label into the window ("U by labels"), else
+// in ub.  Neighbours come from 16-byte ELL records of 16-bit offsets (one load
+// per vertex; rows that do not fit are read from the CSR) or from the CSR.
+// Lanes of a warp take consecutive list entries (on small frontiers 2, 4 or 8
+// lanes share a vertex and split its record), and newly queued vertices are
+// appended with one shared-memory atomic per warp.  One barrier per level.
+// A worklist schedule without level barriers is an option (async_source).
 //
 // Emission writes the sorted row [L cols | s | U cols] to the row pool at an
 // offset taken with one atomicAdd, plus the row's counts and fill count.
