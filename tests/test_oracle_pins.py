@@ -296,3 +296,41 @@ def test_row_subset_matches_full():
             full["L_colidx"][full["L_rowptr"][i]:full["L_rowptr"][i + 1]].tolist()
         assert sub["U_colidx"][sub["U_rowptr"][q]:sub["U_rowptr"][q + 1]].tolist() == \
             full["U_colidx"][full["U_rowptr"][i]:full["U_rowptr"][i + 1]].tolist()
+
+
+def _reach_below(A, i):
+    """Vertices below i that a search from row i can pass through: reachable
+    from i when only vertices below i may be intermediates (plain graph search)."""
+    seen = set(int(w) for w in A.colidx[A.rowptr[i]:A.rowptr[i + 1]] if w != i)
+    stack = [w for w in seen if w < i]
+    reach = set(stack)
+    while stack:
+        v = stack.pop()
+        for w in A.colidx[A.rowptr[v]:A.rowptr[v + 1]]:
+            w = int(w)
+            if w == i or w in seen:
+                continue
+            seen.add(w)
+            if w < i:
+                reach.add(w)
+                stack.append(w)
+    return reach
+
+
+def test_scan_counts_are_the_reach_below_the_row():
+    """The per-row work counts behind the roofline's algorithmic bytes:
+    V_scan(i) = |reach below i| (each such vertex is expanded exactly once by the
+    label-ordered search) and E_scan(i) = the sum of their row lengths; the L row
+    is a subset of that reach."""
+    cases = [synth.random_pattern(n, d, seed=900 + n, diag=bool(n % 2))
+             for n, d in ((12, 0.2), (30, 0.08), (45, 0.05), (60, 0.03))]
+    cases += [synth.grid2d(7, 0.7, seed=3), synth.banded(80, 6, seed=4), load_paper_example()[0]]
+    for A in cases:
+        o = oracle.symbolic(A)
+        deg = np.diff(A.rowptr)
+        for i in range(A.n):
+            R = _reach_below(A, i)
+            assert o["vscan"][i] == len(R), (A.name, i)
+            assert o["escan"][i] == int(sum(deg[v] for v in R)), (A.name, i)
+            Li = set(o["L_colidx"][o["L_rowptr"][i]:o["L_rowptr"][i + 1]].tolist())
+            assert Li <= R
