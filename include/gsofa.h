@@ -185,7 +185,7 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
                              int32_t *d_nnzL, int32_t *d_nnzU, int32_t *d_fill_count, void *stream);
 
 /*
- * Serving (spec extension of the Section 4/5 method): a request loop
+ * Serving (an extension built on the Section 4/5 method): a request loop
  * that factors incoming sparsity patterns with continuous batching.
  * Requests are admitted in arrival order while their projected device memory
  * (CSR copy, per-row workspace, row pool and outputs, label slots of large
