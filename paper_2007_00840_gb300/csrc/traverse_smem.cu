@@ -288,6 +288,28 @@ size_t trav_smem_bytes(int32_t n, int32_t S, int32_t cap, int label16) {
   return label16 ? trav_smem_bytes_t<uint16_t>(n, S, cap) : trav_smem_bytes_t<uint32_t>(n, S, cap);
 }
 
+// Emission of the 16-bit labels, 8 per lane (one 16-byte load): bit q of the
+// result is set iff i + q lies in (lo_excl, hi) and its label marks it: L
+// (below the source) when label < base + 1 + (i + q), i.e. maxId < i + q, U
+// (above it) when label <= top, i.e. reached in this window.  i is a multiple
+// of 8 inside the label array.
+template <bool U>
+__device__ __forceinline__ unsigned label_mask8(const uint16_t* lab, int i, int lo_excl, int hi, uint32_t base,
+                                                uint32_t top) {
+  if (i >= hi) return 0u;
+  const uint4 r = *reinterpret_cast<const uint4*>(lab + i);
+  const uint32_t wd[4] = {r.x, r.y, r.z, r.w};
+  unsigned m = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const uint32_t l = (wd[q >> 1] >> ((q & 1) << 4)) & 0xFFFFu;
+    const int j = i + q;
+    const bool f = U ? (j > lo_excl && j < hi && l <= top) : (j < hi && l < base + 1u + (uint32_t)j);
+    m |= (unsigned)f << q;
+  }
+  return m;
+}
+
 constexpr uint16_t RING_EMPTY = 0xFFFFu;  // vertex ids of the 16-bit tier are <= 65532
 constexpr long long ASYNC_WAIT_CYCLES = 2000000000LL;  // bound of every wait (about 1 s)
 
@@ -804,22 +826,37 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
       atomicAdd(&a.ctr->cyc_trav, (unsigned long long)(t_mid - t_start));
     }
     // ---- emission: counts, pool offset, sorted row
+    // (16-bit labels with U by labels: 8 labels per lane, see label_mask8)
+    constexpr bool VEC = UL && sizeof(LabT) == 2;
     const int perL = (((s + nwarps - 1) / nwarps) + 31) & ~31;
     const int loL = warp * perL, hiL = min(s, loL + perL);
+    const uint32_t top = base + (uint32_t)s;  // largest value of this window
     int cL = 0;
-    for (int i0 = loL; i0 < hiL; i0 += 32) {
-      const int i = i0 + lane;
-      const bool f = i < hiL && (uint32_t)lab[i] < base + 1u + (uint32_t)i;
-      cL += __popc(__ballot_sync(FULL, f));
+    if constexpr (VEC) {
+      for (int i0 = loL; i0 < hiL; i0 += 256)
+        cL += __popc(label_mask8<false>((const uint16_t*)lab, i0 + 8 * lane, -1, hiL, base, top));
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) cL += __shfl_xor_sync(FULL, cL, o);
+    } else {
+      for (int i0 = loL; i0 < hiL; i0 += 32) {
+        const int i = i0 + lane;
+        const bool f = i < hiL && (uint32_t)lab[i] < base + 1u + (uint32_t)i;
+        cL += __popc(__ballot_sync(FULL, f));
+      }
     }
     // U part: labelled vertices above s (UL), else words of the ub bitmap
-    const uint32_t top = base + (uint32_t)s;  // largest value of this window
     const int ws = (s + 1) >> 5;  // first word that can hold a column > s
-    const int nUW = UL ? n - (s + 1) : NW - ws;
-    const int perU = (((nUW + nwarps - 1) / nwarps) + 31) & ~31;
-    const int loU = (UL ? s + 1 : ws) + warp * perU, hiU = min(UL ? n : NW, loU + perU);
+    const int us = (s + 1) & ~7;  // vector scan: first aligned label block that can hold a column > s
+    const int nUW = VEC ? n - us : UL ? n - (s + 1) : NW - ws;
+    const int perU = VEC ? (((nUW + nwarps - 1) / nwarps) + 7) & ~7 : (((nUW + nwarps - 1) / nwarps) + 31) & ~31;
+    const int loU = (VEC ? us : UL ? s + 1 : ws) + warp * perU, hiU = min(UL ? n : NW, loU + perU);
     int cU = 0;
-    if (UL) {
+    if constexpr (VEC) {
+      for (int i0 = loU; i0 < hiU; i0 += 256)
+        cU += __popc(label_mask8<true>((const uint16_t*)lab, i0 + 8 * lane, s, hiU, base, top));
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) cU += __shfl_xor_sync(FULL, cU, o);
+    } else if (UL) {
       for (int i0 = loU; i0 < hiU; i0 += 32) {
         const int i = i0 + lane;
         cU += __popc(__ballot_sync(FULL, i < hiU && (uint32_t)lab[i] <= top));
@@ -862,7 +899,38 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     __syncthreads();
     const long long off = s_off;
     const int nL = s_nL;
-    if (off >= 0) {
+    if (VEC && off >= 0) {
+      // 8 labels per lane; lanes hold consecutive blocks, so a warp scan of the
+      // per-lane counts keeps the row sorted
+      int pos = s_wcL[warp];
+      for (int i0 = loL; i0 < hiL; i0 += 256) {
+        const int i = i0 + 8 * lane;
+        unsigned m = label_mask8<false>((const uint16_t*)lab, i, -1, hiL, base, top);
+        const int c = __popc(m);
+        const int inc = warp_incl_scan(c, lane);
+        long long p = off + pos + (inc - c);
+        while (m) {
+          const int q = __ffs(m) - 1;
+          m &= m - 1u;
+          a.pool[p++] = (uint32_t)(i + q);
+        }
+        pos += __shfl_sync(FULL, inc, 31);
+      }
+      pos = s_wcU[warp];
+      for (int i0 = loU; i0 < hiU; i0 += 256) {
+        const int i = i0 + 8 * lane;
+        unsigned m = label_mask8<true>((const uint16_t*)lab, i, s, hiU, base, top);
+        const int c = __popc(m);
+        const int inc = warp_incl_scan(c, lane);
+        long long p = off + nL + 1 + pos + (inc - c);
+        while (m) {
+          const int q = __ffs(m) - 1;
+          m &= m - 1u;
+          a.pool[p++] = (uint32_t)(i + q);
+        }
+        pos += __shfl_sync(FULL, inc, 31);
+      }
+    } else if (!VEC && off >= 0) {
       int pos = s_wcL[warp];
       for (int i0 = loL; i0 < hiL; i0 += 32) {
         const int i = i0 + lane;
@@ -872,7 +940,9 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
         pos += __popc(m);
       }
     }
-    if (UL) {
+    if (VEC) {
+      // written above
+    } else if (UL) {
       if (off >= 0) {
         int pos = s_wcU[warp];
         for (int i0 = loU; i0 < hiU; i0 += 32) {
