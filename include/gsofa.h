@@ -193,7 +193,10 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
  * requests waiting at that moment (up to max_batch) as one multi-matrix batch.
  * A slot launches as soon as it is free, so the next batch queues on the GPU
  * behind the running one and their phases overlap (opts.max_ctas can split
- * the GPU between slots instead).
+ * the GPU between slots instead).  A request whose label slots alone would
+ * exceed the cap runs alone with as many slots as the cap leaves room for
+ * (space-budget mode: fewer sources in flight, same result); one that does
+ * not fit even with one slot is refused with GSOFA_E_NOMEM.
  */
 typedef struct gsofa_server gsofa_server;
 

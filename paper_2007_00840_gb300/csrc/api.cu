@@ -1490,6 +1490,8 @@ int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, c
   return run_batch(c, count, n, rp, ci, o, st, outs, true);
 }
 
+int64_t global_slot_bytes(int32_t n) { return slot_bytes(((int64_t)n + 1023) / 1024 * 1024); }
+
 int64_t global_tier_bytes(int32_t n, const gsofa_options* opts) {
   int err = GSOFA_OK;
   Ctx* c = get_ctx(&err);

@@ -161,6 +161,8 @@ int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, c
 int device_sms();
 // Bytes of the global-tier slots a single-matrix call of order n would hold.
 int64_t global_tier_bytes(int32_t n, const gsofa_options* opts);
+// Bytes of one global-tier slot for order n.
+int64_t global_slot_bytes(int32_t n);
 void detach_result_stream(gsofa_result* r);
 int32_t smem_tier_max_order();
 int wait_stream(cudaStream_t st);  // bounded wait; GSOFA_OK / GSOFA_E_TIMEOUT / GSOFA_E_CUDA

@@ -39,6 +39,7 @@ struct Request {
   const int32_t* h_ci = nullptr;
   int32_t* own = nullptr;           // server copy of a host CSR (rowptr then colidx)
   int64_t projected = 0;
+  int64_t budget = 0;               // space-budget mode: mem_budget_bytes of this request (0: server default)
   Clock::time_point t_submit, t_done;
   bool done = false;
   int status = GSOFA_OK;
@@ -134,16 +135,41 @@ void worker_loop(gsofa_server* S, int slot) {
       r->ci = r->own + r->n + 1;
     }
     const int k = (int)take.size();
-    ns.resize(k);
-    rps.resize(k);
-    cis.resize(k);
     outs.assign(k, gsofa_result());
+    // requests admitted in space-budget mode run alone with their own budget;
+    // the others run as one batch
+    ns.clear();
+    rps.clear();
+    cis.clear();
+    std::vector<int> in_batch;
     for (int i = 0; i < k; i++) {
-      ns[i] = take[i]->n;
-      rps[i] = take[i]->rp;
-      cis[i] = take[i]->ci;
+      if (take[i]->budget > 0) continue;
+      in_batch.push_back(i);
+      ns.push_back(take[i]->n);
+      rps.push_back(take[i]->rp);
+      cis.push_back(take[i]->ci);
     }
-    if (rc == GSOFA_OK) rc = batch_transient(k, ns.data(), rps.data(), cis.data(), &S->cfg.opts, st, outs.data());
+    int64_t launches = 0;
+    if (rc == GSOFA_OK && !in_batch.empty()) {
+      std::vector<gsofa_result> bo(in_batch.size());
+      rc = batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &S->cfg.opts, st, bo.data());
+      if (rc == GSOFA_OK) {
+        launches += bo[0].stats.kernel_launches;  // the batch's total
+        for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
+      }
+    }
+    for (int i = 0; rc == GSOFA_OK && i < k; i++) {
+      if (take[i]->budget == 0) continue;
+      gsofa_options o = S->cfg.opts;
+      o.mem_budget_bytes = take[i]->budget;
+      const int32_t n1 = take[i]->n;
+      const int32_t* rp1 = take[i]->rp;
+      const int32_t* ci1 = take[i]->ci;
+      rc = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i]);
+      if (rc == GSOFA_OK) launches += outs[i].stats.kernel_launches;
+    }
+    if (rc != GSOFA_OK)
+      for (int i = 0; i < k; i++) gsofa_free(&outs[i]);
     if (rc == GSOFA_OK) rc = wait_stream(st);  // results complete
     // the slot stream outlives nothing the caller holds: results are freed stream-less
     for (int i = 0; rc == GSOFA_OK && i < k; i++) detach_result_stream(&outs[i]);
@@ -155,7 +181,7 @@ void worker_loop(gsofa_server* S, int slot) {
       }
     std::lock_guard<std::mutex> lk(S->mu);
     S->batches++;
-    if (rc == GSOFA_OK && k > 0) S->launches += outs[0].stats.kernel_launches;  // the batch's total
+    if (rc == GSOFA_OK) S->launches += launches;
     for (int i = 0; i < k; i++) {
       Request* r = take[i];
       r->t_done = now;
@@ -269,6 +295,17 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
   }
   if (r->nnz < 0) { delete r; return GSOFA_E_INVAL; }
   r->projected = projected_bytes(S, n, r->nnz, !on_device);
+  if (r->projected > S->cfg.mem_cap_bytes && n > S->smem_max_n) {
+    // space-budget mode (the concurrent-source budget of Section 5, Eq. 1): run
+    // the request with as many global-tier slots as the cap leaves room for
+    const int64_t base = r->projected - global_tier_bytes(n, &S->cfg.opts);
+    const int64_t one = global_slot_bytes(n);
+    const int64_t slots = one > 0 ? (S->cfg.mem_cap_bytes - base) / one : 0;
+    if (slots >= 1) {
+      r->budget = 2 * slots * one;  // the global tier takes half of mem_budget_bytes
+      r->projected = base + slots * one;
+    }
+  }
   if (r->projected > S->cfg.mem_cap_bytes) { delete r; return GSOFA_E_NOMEM; }
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) { delete r; return GSOFA_E_INVAL; }

@@ -88,3 +88,35 @@ def test_admission_cap_busy_and_oversize():
     assert ei.value.code == -2
     assert srv.stats()["peak_mem_in_use"] <= 64 << 20
     srv.close()
+
+
+def test_space_budget_admission():
+    """A request whose default global-tier slots exceed the memory cap is admitted
+    with fewer slots (the concurrent-source budget of Section 5, Eq. 1) instead of
+    being refused, and its result is unchanged."""
+    import torch
+    import paper_2007_00840_gb300 as gs
+    big = synth.grid2d_nd(300, 0.8, seed=5)   # n = 90,000: global tier
+    dev = to_device(big)
+    alone = gs.symbolic_device(*dev).to_host()
+    small = [synth.batch_mix_one(m, seed=50 + m, n_lo=200, n_hi=2000) for m in range(6)]
+    sdev = [to_device(A) for A in small]
+    salone = [gs.symbolic_device(*d).to_host() for d in sdev]
+    torch.cuda.synchronize()
+    cap = 1536 << 20
+    srv = gs.Server(mem_cap_bytes=cap, streams=2)
+    t_big = srv.submit(*dev)
+    tickets = [srv.submit(*d) for d in sdev]
+    r, _ = srv.wait(t_big)
+    h = r.to_host()
+    for f in FIELDS:
+        assert np.array_equal(getattr(h, f), getattr(alone, f)), f
+    for t, a in zip(tickets, salone):
+        r, _ = srv.wait(t)
+        h = r.to_host()
+        for f in FIELDS:
+            assert np.array_equal(getattr(h, f), getattr(a, f)), f
+    st = srv.stats()
+    assert st["completed"] == 7 and st["failed"] == 0
+    assert st["peak_mem_in_use"] <= cap
+    srv.close()
