@@ -71,7 +71,11 @@ typedef struct gsofa_options {
                                     (default 0: one full wave) */
     int32_t frontier_order;      /* 0: automatic; 1: breadth-first levels (shared-memory tier wherever the
                                     maxId array fits on chip); 2: by increasing maxId class (warp tier).
-                                    Same result; with autotune = 1 the faster one is kept per shape */
+                                    Same result.  Automatic: when every source fits on chip, the first
+                                    call for a matrix (the same n and device buffers, or n and nnz for
+                                    host input) runs breadth-first and later calls switch to class
+                                    order if its frontiers averaged under 128 vertices per level;
+                                    with autotune = 1 both are timed once per shape instead */
     int32_t label_bits;          /* shared-memory tier maxId width: 0 automatic (16 when n <= 65533), 16 or 32 */
     int32_t expand_mode;         /* shared-memory tier row access: 0 automatic, 1 CSR row slots per lane,
                                     2 CSR edge-balanced (a warp flattens its rows' entries), 3 16-byte

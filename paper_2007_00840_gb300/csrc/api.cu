@@ -46,8 +46,11 @@ struct Ctx {
   std::mutex hmu;
   std::map<int32_t, long long> pool_hint;
   double rows_ratio = 0.0;  // largest pool entries per row seen (nnz(L+U) + 1 per row)
+  std::atomic<int64_t> free_bytes{-1};  // device memory free when first asked (slot sizing)
   // single-matrix autotune: faster frontier order by (n, nnz)
   std::map<std::pair<int32_t, int64_t>, int> order_tuned;
+  // single-matrix default: frontier order chosen from the first call's mean frontier size
+  std::map<std::pair<int32_t, int64_t>, int> order_learned;
 };
 
 std::mutex g_ctx_mu;
@@ -220,14 +223,22 @@ int64_t slot_bytes(int64_t cap) { return cap * 16 + 2 * (cap / 8 + cap / 256); }
 int64_t global_budget(const Ctx* c, const gsofa_options& o) {
   if (o.mem_budget_bytes > 0) return o.mem_budget_bytes / 2;
   int64_t b = (int64_t)96 << 30;
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-    const int64_t held = c->g_lab ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
-    const int64_t half = ((int64_t)fr + held) / 2;
-    if (half < b) b = half;
-  } else {
-    cudaGetLastError();
+  // free memory is asked once per device (the query costs a few hundred
+  // microseconds, as much as a whole small factorisation)
+  int64_t fr = c->free_bytes.load();
+  if (fr < 0) {
+    size_t f = 0, tot = 0;
+    if (cudaMemGetInfo(&f, &tot) == cudaSuccess) {
+      const int64_t held = c->g_lab ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
+      fr = (int64_t)f + held;
+      int64_t expect = -1;
+      const_cast<Ctx*>(c)->free_bytes.compare_exchange_strong(expect, fr);
+    } else {
+      cudaGetLastError();
+      fr = 2 * b;
+    }
   }
+  if (fr / 2 < b) b = fr / 2;
   return b;
 }
 
@@ -1598,25 +1609,53 @@ void gsofa_free(gsofa_result* res) {
   std::memset(res, 0, sizeof(*res));
 }
 
-int gsofa_symbolic_device(int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx,
-                          const gsofa_options* opt, void* stream, gsofa_result* out) {
-  if (!out) return GSOFA_E_INVAL;
-  zero_result(out);
-  out->err_detail = -1;
-  gsofa_options o;
-  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
-  if (n < 0 || !d_rowptr || (n > 0 && !d_colidx)) return GSOFA_E_INVAL;
-  if (n > INT32_MAX - 2) return GSOFA_E_INVAL;
-  int err = GSOFA_OK;
-  Ctx* c = get_ctx(&err);
-  if (!c) return err;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (o.autotune && o.frontier_order == 0 && n > 0) {
-    // time both frontier orders once for this shape and keep the faster
-    int32_t nnz = 0;
-    if (cudaMemcpyAsync(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+namespace {
+
+// One matrix: pick the frontier order (learned default or autotune), then run.
+// nnz < 0 (device input): the learned order is kept per (n, device buffers),
+// so no read is needed; autotune reads nnz and keeps its choice per (n, nnz).
+int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx, gsofa_options o,
+               cudaStream_t st, gsofa_result* out, int64_t nnz_known) {
+  const bool learn = !o.autotune && o.frontier_order == 0 && o.smem_max_source == 0 && n > 0 &&
+                     n <= smem_tier_max_order();
+  const bool tune = o.autotune && o.frontier_order == 0 && n > 0;
+  int64_t nnz = nnz_known;
+  if (tune && nnz < 0) {
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         wait_stream(st) != GSOFA_OK)
       return GSOFA_E_CUDA;
+    nnz = v;
+  }
+  if (learn) {
+    // Every source fits the shared-memory tier.  Its breadth-first levels pay a
+    // barrier each, so when the first call of this shape found small frontiers
+    // (fewer than 128 vertices per level on average: long, thin searches such as
+    // 2D grids and banded patterns) later calls use the class-ordered warp tier.
+    const int64_t tag = nnz >= 0 ? nnz
+                                 : (int64_t)(mix64((uint64_t)(uintptr_t)d_rowptr, (uint64_t)(uintptr_t)d_colidx) |
+                                             (1ull << 62));
+    const std::pair<int32_t, int64_t> key(n, tag);
+    int learned = 0;
+    {
+      std::lock_guard<std::mutex> lk(c->hmu);
+      auto it = c->order_learned.find(key);
+      if (it != c->order_learned.end()) learned = it->second;
+    }
+    if (learned) {
+      o.frontier_order = learned;
+      return run_device(c, n, d_rowptr, d_colidx, o, st, out);
+    }
+    const int rc = run_device(c, n, d_rowptr, d_colidx, o, st, out);
+    if (rc == GSOFA_OK && out->stats.levels > 0) {
+      const double per_level = (double)out->stats.vertices_expanded / (double)out->stats.levels;
+      std::lock_guard<std::mutex> lk(c->hmu);
+      c->order_learned[key] = per_level < 128.0 ? 2 : 1;
+    }
+    return rc;
+  }
+  if (tune) {
+    // time both frontier orders once for this shape and keep the faster
     const std::pair<int32_t, int64_t> key(n, nnz);
     int best = 0;
     {
@@ -1648,6 +1687,24 @@ int gsofa_symbolic_device(int32_t n, const int32_t* d_rowptr, const int32_t* d_c
   return run_device(c, n, d_rowptr, d_colidx, o, st, out);
 }
 
+}  // namespace
+
+int gsofa_symbolic_device(int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx,
+                          const gsofa_options* opt, void* stream, gsofa_result* out) {
+  if (!out) return GSOFA_E_INVAL;
+  zero_result(out);
+  out->err_detail = -1;
+  gsofa_options o;
+  if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
+  if (n < 0 || !d_rowptr || (n > 0 && !d_colidx)) return GSOFA_E_INVAL;
+  if (n > INT32_MAX - 2) return GSOFA_E_INVAL;
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return err;
+  cudaStream_t st = (cudaStream_t)stream;
+  return run_single(c, n, d_rowptr, d_colidx, o, st, out, -1);
+}
+
 int gsofa_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colidx, const gsofa_options* opt,
                    gsofa_result* out) {
   if (!out) return GSOFA_E_INVAL;
@@ -1675,7 +1732,7 @@ int gsofa_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colidx, cons
                                          st) != cudaSuccess)) {
     rc = GSOFA_E_CUDA;
   } else {
-    rc = run_device(c, n, d_rp, d_ci, o, st, &dres);
+    rc = run_single(c, n, d_rp, d_ci, o, st, &dres, nnz);
   }
   if (rc == GSOFA_OK) {
     out->n = n;

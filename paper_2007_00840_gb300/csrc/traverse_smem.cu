@@ -820,9 +820,11 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
     }
 
     long long t_mid = 0;
+    // levels and expansions are always counted (the library uses their ratio,
+    // the mean frontier size, to pick the frontier order of later calls)
+    if (tid == 0) atomicAdd(&a.ctr->levels, (unsigned long long)(L - 1));
     if (a.collect_stats && tid == 0) {
       t_mid = clock64();
-      atomicAdd(&a.ctr->levels, (unsigned long long)(L - 1));
       atomicAdd(&a.ctr->cyc_trav, (unsigned long long)(t_mid - t_start));
     }
     // ---- emission: counts, pool offset, sorted row
@@ -976,16 +978,14 @@ __global__ void __launch_bounds__(1024, 1) trav_smem_kernel(TravArgs a) {
   }
 
   if (bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
-  if (a.collect_stats) {
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      n_exp += __shfl_xor_sync(FULL, n_exp, o);
-      n_edge += __shfl_xor_sync(FULL, n_edge, o);
-    }
-    if (lane == 0) {
-      atomicAdd(&a.ctr->expansions, n_exp);
-      atomicAdd(&a.ctr->edges, n_edge);
-    }
+  for (int o = 16; o >= 1; o >>= 1) {
+    n_exp += __shfl_xor_sync(FULL, n_exp, o);
+    n_edge += __shfl_xor_sync(FULL, n_edge, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&a.ctr->expansions, n_exp);
+    if (a.collect_stats) atomicAdd(&a.ctr->edges, n_edge);
   }
 }
 
