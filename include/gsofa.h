@@ -53,20 +53,25 @@ extern "C" {
 /* Tuning knobs.  Zero in any field selects the default. */
 typedef struct gsofa_options {
     int32_t chunk_size;          /* rows per supernode chunk = maximum supernode size (default 128, Section 5) */
-    int32_t threads_per_source;  /* CTA size of the traversal kernels (default 512; 128..1024, multiple of 32) */
+    int32_t threads_per_source;  /* CTA size of the shared-memory traversal (default: the size with the most
+                                    resident threads, 512 x 2 per SM for n = 32,768; 64..1024, multiple of 32) */
     int32_t smem_max_source;     /* sources below this use shared-memory labels (default 0: as many as fit;
                                     -1: none, every source uses the global-memory tier) */
-    int32_t max_concurrent;      /* global-label tier: concurrent source slots (default: one per SM) */
-    int64_t mem_budget_bytes;    /* cap on library working memory per call (default: none) */
+    int32_t max_concurrent;      /* global-label tier: concurrent source slots, one warp each (default: 32 per SM
+                                    within the memory budget) */
+    int64_t mem_budget_bytes;    /* global-label tier: half of it bounds the slots' memory (default: half of
+                                    the device memory free at first use, at most 96 GiB) */
     int32_t fill_first;          /* 1: skip lowering the maxId of a vertex already known to be a fill
                                     (the optional "line 9.5" of Section 4); same result */
     int32_t collect_stats;       /* 1: record per-phase CUDA-event times and work counters */
     int32_t validate;            /* 0 or 1: check the CSR on the device first (default 1); 2: skip */
-    int32_t autotune;            /* gsofa_batch: 1 = time candidate launch shapes once per batch shape
-                                    (block size, frontier list capacity, work items per fetch) and keep
-                                    the fastest; 0 = heuristic shape */
+    int32_t autotune;            /* 1 = time candidates once and keep the fastest: gsofa_batch per batch shape
+                                    (kernel, block size, CTAs or warps per SM, frontier list capacity,
+                                    work items per fetch); single matrices per (n, nnz) (frontier
+                                    order).  0 = heuristic choices */
     int32_t work_chunk;          /* work items a CTA takes per fetch (default 1) */
-    int32_t list_capacity;       /* frontier list entries kept in shared memory (default: as many as fit) */
+    int32_t list_capacity;       /* frontier list entries kept in shared memory (default 2,048, fewer if the
+                                    occupancy needs it; the rest spills to global memory) */
     int32_t max_ctas;            /* cap on traversal CTAs per launch, so concurrent launches share the GPU
                                     (default 0: one full wave) */
     int32_t frontier_order;      /* 0: automatic; 1: breadth-first levels (shared-memory tier wherever the
@@ -88,7 +93,9 @@ typedef struct gsofa_options {
     int32_t reserved[2];
 } gsofa_options;
 
-/* Per-call statistics (filled when options.collect_stats == 1). */
+/* Per-call statistics.  Times, cycles and edges_scanned are filled when
+ * options.collect_stats == 1; kernel_launches, pool_retries, levels and the
+ * shared-memory tier's vertices_expanded always. */
 typedef struct gsofa_stats {
     float ms_validate, ms_traverse, ms_emit, ms_supernode, ms_total;
     float ms_traverse_smem, ms_traverse_global;
