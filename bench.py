@@ -1,11 +1,12 @@
 #!/usr/bin/env python3
-"""Benchmark: GB300 symbolic LU (gSoFa method) on the 32^3 7-point grid workload.
+"""Benchmark: GB300 symbolic LU (gSoFa method); default workload the 1024^2
+nested-dissection 5-point grid (n = 1,048,576), the largest single-matrix workload.
 
 One step = one pass of the whole hot path over the matrix: CSR validation,
 maxId traversal of every source row, supernode detection, L/U CSR emission
 (one ``gsofa_symbolic_device`` call on device-resident input).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload grid3d|grid2d]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload nd1024|grid3d|grid2d|batch512|served]
 
 Prints ONE JSON line (rank 0).  ``value`` is nnz(L+U) per second over all
 ranks (each rank factors its own replica: the method needs no exchange);
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="nd1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="served: stream length")
@@ -80,6 +81,39 @@ def sum_over_ranks(x: float, world: int, device) -> float:
     t = torch.tensor([x], device=device, dtype=torch.float64)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
     return float(t.item())
+
+
+L2_NOTE = "GPU arm: L2 flushed between steps (256 MB write)"
+
+
+def workload_config(name, A, nnz_lu, extra, world):
+    """The `config` object of both arms (the GPU line and the reference line)."""
+    return {"workload": name, "n": int(A.n), "nnz_A": int(A.nnz), "nnz_LU": int(nnz_lu), "options": extra,
+            "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
+
+
+def kernel_source_digest():
+    """SHA-256 of the traversal kernel sources; a stored DRAM-traffic figure is
+    reported only for the kernel build it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2007_00840_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("traverse_") or f == "internal.cuh":
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def stored_traffic(name):
+    """DRAM bytes per traversal launch from profiles/traffic.json, if it was
+    measured on the current kernel sources (else None)."""
+    try:
+        ent = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(name)
+    except Exception:
+        return None
+    if not isinstance(ent, dict) or ent.get("kernel_sources_sha256") != kernel_source_digest():
+        return None
+    return ent.get("bytes_per_launch")
 
 
 def algorithmic_bytes(vscan, escan, nnz_rows, n):
@@ -155,23 +189,28 @@ def cpu_baseline(A, stride: int, min_wall: float = 1.0):
     return {"value": nnz / dt, "unit": "nnz(L+U)/s", "cores": cores, "kind": "oracle",
             "sample": f"every {stride}th row ({rows.size} of {A.n} rows) x {reps} passes, "
                       f"{nnz} nnz(L+U), {dt:.2f} s wall",
-            "rows_per_s": reps * rows.size / dt}
+            "rows_per_s": reps * rows.size / dt, "nnz": nnz // reps}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only), on the
+    same rows as the GPU arm (every row of the workload)."""
     import synth
     if rank != 0:
         return 0
+    if args.workload in ("batch512", "served"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm times single-matrix workloads; use --workload nd1024|grid3d|grid2d"}))
+        return 0
     k, name = WORKLOADS[args.workload]
     A = synth.config(k)
-    stride = 4 if args.workload == "grid3d" else 1
+    extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
     for _ in range(args.warmup):
-        cpu_baseline(A, stride * 4, min_wall=0.0)
+        cpu_baseline(A, 16, min_wall=0.0)
     vals, rows = [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cb = cpu_baseline(A, stride, min_wall=0.25)
+        cb = cpu_baseline(A, 1, min_wall=0.0)
         vals.append(cb["value"])
         rows.append(cb["rows_per_s"])
     wall = time.perf_counter() - t0
@@ -181,7 +220,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded)",
-        "config": {"workload": name, "n": A.n, "nnz_A": A.nnz, "l2": "n/a (CPU)"},
+        "config": workload_config(name, A, cb["nnz"], extra, world),
         "cpu_baseline": {"value": v, "unit": "nnz(L+U)/s", "cores": cb["cores"], "kind": "oracle",
                          "sample": cb["sample"]},
         "e2e": {"value": v, "unit": "nnz(L+U)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -310,13 +349,8 @@ def main():
     alg = algorithmic_bytes(orc["vscan"], orc["escan"], nnz_rows, n)
     t_trav = statistics.mean(trav_ms) / 1000.0
     achieved = alg / t_trav / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path) and not extra:  # counters were taken with the default options
-        try:
-            traffic = json.load(open(tr_path)).get(name)
-        except Exception:
-            traffic = None
+    # DRAM bytes per launch from an ncu capture of this kernel source (default options only)
+    traffic = stored_traffic(name) if not extra else None
 
     # the dominant traversal tier of this matrix
     if stats0["ms_traverse_global"] > stats0["ms_traverse_smem"]:
@@ -328,8 +362,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_dev / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded)",
-        "config": {"workload": name, "n": n, "nnz_A": A.nnz, "nnz_LU": int(nnz_step), "options": extra,
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "config": workload_config(name, A, nnz_step, extra, world),
         "rows_per_s": rows_per_s,
         "wall_s": wall,
         "e2e": e2e,
@@ -512,8 +545,7 @@ def run_served_bench(args, rank, world, local):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     gbuild.build()
     dev = torch.device("cuda", local)
-    small = synth.config(3)
-    big = [synth.grid2d_nd(512, 0.8, seed=synth.config_seed(4) + j) for j in range(4)]
+    small, big = synth.served_pool()
     pool = small + big
     dpool = [(torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev)) for A in pool]
     # batched throughput of the small mix sets the arrival rate
@@ -542,9 +574,7 @@ def run_served_bench(args, rank, world, local):
     # saturated served throughput: a burst of requests submitted at once
     nreq = args.requests
     burst = min(2000, nreq)
-    which_b = np.where(np.random.default_rng(5).random(burst) < 0.02,
-                       len(small) + np.random.default_rng(6).integers(0, len(big), burst),
-                       np.random.default_rng(7).integers(0, len(small), burst))
+    which_b, _ = synth.served_choices(burst, len(small), len(big), seed=5)
     srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30)
     t0 = time.perf_counter()
     tk = [srv.submit(*dpool[int(k)]) for k in which_b]
@@ -553,17 +583,11 @@ def run_served_bench(args, rank, world, local):
     sat_rps = burst / (time.perf_counter() - t0)
     srv.close()
     lam = args.rate_frac * sat_rps
-    rng = np.random.default_rng(4)
-    which = np.where(rng.random(nreq) < 0.02, len(small) + rng.integers(0, len(big), nreq),
-                     rng.integers(0, len(small), nreq))
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, nreq))
-    # reference results (each pattern alone) for a sample of requests
-    check_idx = set(range(0, nreq, 211))
-    ref = {}
-    for i in sorted(check_idx):
-        k = int(which[i])
-        if k not in ref:
-            ref[k] = gs.symbolic_device(*dpool[k]).to_host()
+    which, arrivals = synth.served_choices(nreq, len(small), len(big), seed=4)
+    arrivals = arrivals / lam
+    # every pattern of the pool run alone: each served result is compared with it
+    # on the device after the stream (the comparison is outside the latency)
+    ref = [gs.symbolic_device(*d) for d in dpool]
     torch.cuda.synchronize(dev)
     srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30, opts=gs.options())
     sampler = ClockSampler(local)
@@ -577,16 +601,13 @@ def run_served_bench(args, rank, world, local):
         tickets.append(srv.submit(*dpool[int(which[i])]))
     mismatches = 0
     for i, t in enumerate(tickets):
-        keep = i in check_idx
-        r, _ = srv.wait(t, keep_result=keep)
-        if keep:
-            h = r.to_host()
-            g = ref[int(which[i])]
-            for f in ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start"):
-                if not np.array_equal(getattr(h, f), getattr(g, f)):
-                    mismatches += 1
-                    break
-            del r
+        r, _ = srv.wait(t, keep_result=True)
+        g = ref[int(which[i])]
+        for f in ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start"):
+            if not torch.equal(getattr(r, f), getattr(g, f)):
+                mismatches += 1
+                break
+        del r
     wall = time.perf_counter() - start
     clocks = sampler.stop()
     st = srv.stats()
@@ -642,7 +663,7 @@ def run_served_bench(args, rank, world, local):
         "gpu_launches": int(launches_all), "latency_scope": "rank 0" if world > 1 else "all requests",
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "batches": st["batches"],
         "peak_projected_mem_bytes": st["peak_mem_in_use"], "completed": st["completed"], "failed": st["failed"],
-        "checked_against_alone": len(check_idx), "mismatches": mismatches, "wall_s": wall, "clocks": clocks,
+        "checked_against_alone": nreq, "mismatches": mismatches, "wall_s": wall, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

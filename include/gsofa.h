@@ -182,11 +182,15 @@ int gsofa_batch(int32_t count, const int32_t *n, const int32_t *const *d_rowptr,
  *   d_rowptr, d_colidx device CSR of A (borrowed, validated on the device)
  *   d_nnzL, d_nnzU     device int32[n]: nnz(L(i,:)) and nnz(U(i,:)) (diagonal included)
  *   d_fill_count       device int32[n]: fill-ins of row i (as gsofa_result.fill_count)
- *   stream             cudaStream_t; the call waits for its own work before returning
+ *   stream             cudaStream_t.  Every call copies its counters to the host
+ *                      and waits until all work queued on `stream` has finished
+ *                      before it returns (a bounded wait, GSOFA_E_TIMEOUT).
  * Scratch: a fixed array of GSOFA_NOALLOC_SCRATCH_BYTES in device memory, held
  * by every GPU that loads the library until the process exits.  The first call
  * on a device looks up that array's device address (once per device); make the
- * first call before any stream capture.  All calls share the array, so calls
+ * first call before any stream capture.  Near GSOFA_NOALLOC_MAX_N the frontier
+ * overflow lists of fewer CTAs fit the array, so the launch uses fewer CTAs;
+ * GSOFA_E_NOMEM if not even one fits.  All calls share the array, so calls
  * that overlap on the GPU (concurrent streams or host threads) race; serialise
  * them.  No cudaMalloc, cudaFree or other allocating routine is called.
  */

@@ -200,7 +200,8 @@ cudaError_t launch_compact(int32_t n, const uint32_t* pool, const int64_t* row_o
   if (n <= 0) return cudaSuccess;
   const int block = 256;
   long long grid = ((long long)n * 32 + block - 1) / block;
-  if (grid > 152 * 16) grid = 152 * 16;
+  const long long cap = 16LL * device_sms();  // 16 resident CTAs of 256 threads per SM
+  if (cap > 0 && grid > cap) grid = cap;
   compact_kernel<<<(int)grid, block, 0, st>>>(n, pool, row_off, row_nL, row_nU, L_rowptr, U_rowptr,
                                               L_colidx, U_colidx);
   return cudaGetLastError();

@@ -19,6 +19,7 @@ namespace gsofa {
 namespace {
 
 static_assert(GSOFA_NOALLOC_SCRATCH_BYTES >= 4096, "scratch too small");
+static_assert(sizeof(DevCounters) <= 256, "the counters block must fit ahead of the overflow lists");
 
 // Scratch of this entry point: [0, 256) counters, then frontier overflow lists.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GSOFA_NOALLOC_SCRATCH_BYTES];

@@ -120,8 +120,10 @@ void worker_loop(gsofa_server* S, int slot) {
       }
     }
     // host inputs: copy into pooled device memory on this slot's stream
-    int rc = GSOFA_OK;
-    for (Request* r : take) {
+    const int k = (int)take.size();
+    std::vector<int> rcs(k, GSOFA_OK);
+    for (int i = 0; i < k; i++) {
+      Request* r = take[i];
       if (!r->h_rp) continue;
       const size_t words = (size_t)r->n + 1 + (size_t)r->nnz;
       if (cudaMallocFromPoolAsync((void**)&r->own, 4 * (words > 0 ? words : 1), S->mpool, st) != cudaSuccess ||
@@ -129,12 +131,12 @@ void worker_loop(gsofa_server* S, int slot) {
           (r->nnz > 0 && cudaMemcpyAsync(r->own + r->n + 1, r->h_ci, 4 * (size_t)r->nnz, cudaMemcpyHostToDevice,
                                          st) != cudaSuccess)) {
         cudaGetLastError();
-        rc = GSOFA_E_NOMEM;
+        rcs[i] = GSOFA_E_NOMEM;
+        continue;
       }
       r->rp = r->own;
       r->ci = r->own + r->n + 1;
     }
-    const int k = (int)take.size();
     outs.assign(k, gsofa_result());
     // requests admitted in space-budget mode run alone with their own budget;
     // the others run as one batch
@@ -143,36 +145,47 @@ void worker_loop(gsofa_server* S, int slot) {
     cis.clear();
     std::vector<int> in_batch;
     for (int i = 0; i < k; i++) {
-      if (take[i]->budget > 0) continue;
+      if (take[i]->budget > 0 || rcs[i] != GSOFA_OK) continue;
       in_batch.push_back(i);
       ns.push_back(take[i]->n);
       rps.push_back(take[i]->rp);
       cis.push_back(take[i]->ci);
     }
     int64_t launches = 0;
-    if (rc == GSOFA_OK && !in_batch.empty()) {
-      std::vector<gsofa_result> bo(in_batch.size());
-      rc = batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &S->cfg.opts, st, bo.data());
-      if (rc == GSOFA_OK) {
-        launches += bo[0].stats.kernel_launches;  // the batch's total
-        for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
-      }
-    }
-    for (int i = 0; rc == GSOFA_OK && i < k; i++) {
-      if (take[i]->budget == 0) continue;
-      gsofa_options o = S->cfg.opts;
-      o.mem_budget_bytes = take[i]->budget;
+    auto run_alone = [&](int i, const gsofa_options& o) {
       const int32_t n1 = take[i]->n;
       const int32_t* rp1 = take[i]->rp;
       const int32_t* ci1 = take[i]->ci;
-      rc = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i]);
-      if (rc == GSOFA_OK) launches += outs[i].stats.kernel_launches;
+      rcs[i] = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i]);
+      if (rcs[i] == GSOFA_OK) launches += outs[i].stats.kernel_launches;
+    };
+    if (!in_batch.empty()) {
+      std::vector<gsofa_result> bo(in_batch.size());
+      const int brc =
+          batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &S->cfg.opts, st, bo.data());
+      if (brc == GSOFA_OK) {
+        launches += bo[0].stats.kernel_launches;  // the batch's total
+        for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
+      } else if (brc == GSOFA_E_INVAL && in_batch.size() > 1) {
+        // a malformed pattern rejects the whole batch: run the members one by
+        // one so that only the offending request fails, as it would alone
+        for (int i : in_batch) run_alone(i, S->cfg.opts);
+      } else {
+        for (int i : in_batch) rcs[i] = brc;
+      }
     }
-    if (rc != GSOFA_OK)
-      for (int i = 0; i < k; i++) gsofa_free(&outs[i]);
-    if (rc == GSOFA_OK) rc = wait_stream(st);  // results complete
-    // the slot stream outlives nothing the caller holds: results are freed stream-less
-    for (int i = 0; rc == GSOFA_OK && i < k; i++) detach_result_stream(&outs[i]);
+    for (int i = 0; i < k; i++) {
+      if (take[i]->budget == 0 || rcs[i] != GSOFA_OK) continue;
+      gsofa_options o = S->cfg.opts;
+      o.mem_budget_bytes = take[i]->budget;
+      run_alone(i, o);
+    }
+    const int wrc = wait_stream(st);  // results complete
+    for (int i = 0; i < k; i++) {
+      if (rcs[i] == GSOFA_OK && wrc != GSOFA_OK) rcs[i] = wrc;
+      if (rcs[i] != GSOFA_OK) gsofa_free(&outs[i]);
+      else detach_result_stream(&outs[i]);  // results are freed stream-less
+    }
     const Clock::time_point now = Clock::now();
     for (Request* r : take)
       if (r->own) {
@@ -181,12 +194,12 @@ void worker_loop(gsofa_server* S, int slot) {
       }
     std::lock_guard<std::mutex> lk(S->mu);
     S->batches++;
-    if (rc == GSOFA_OK) S->launches += launches;
+    S->launches += launches;
     for (int i = 0; i < k; i++) {
       Request* r = take[i];
       r->t_done = now;
-      r->status = rc;
-      if (rc == GSOFA_OK) {
+      r->status = rcs[i];
+      if (rcs[i] == GSOFA_OK) {
         r->res = outs[i];
         S->completed++;
         S->total_nnz += outs[i].nnz_L + outs[i].nnz_U;

@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "CSR", "splitmix64", "hash3", "unif", "grid2d", "grid3d_extra", "grid2d_nd",
     "nd_permutation", "banded", "near_square_grid", "batch_mix", "random_pattern",
-    "config_seed", "config", "CONFIG_NAMES",
+    "config_seed", "config", "CONFIG_NAMES", "served_pool", "served_choices",
 ]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -363,6 +363,26 @@ def served_request(idx: int, big_n_side: int = 512, big_frac: float = 0.02, seed
         return grid2d_nd(big_n_side, 0.8, sub, name=f"req{idx}_nd{big_n_side}")
     m = int(hash3(s, idx, 13) % np.uint64(1 << 30))
     return batch_mix_one(m, sub)
+
+
+def served_pool(big_count: int = 4, big_n_side: int = 512):
+    """Finite pool behind the served request stream: the 512-matrix mix (drawn
+    with probability 0.98) and ``big_count`` ND grids of side ``big_n_side``
+    (probability 0.02).  Returns (small, big), two lists of CSR."""
+    small = config(3)
+    big = [grid2d_nd(big_n_side, 0.8, seed=config_seed(4) + j, name=f"served_nd{big_n_side}_{j}")
+           for j in range(big_count)]
+    return small, big
+
+
+def served_choices(count: int, n_small: int, n_big: int, seed: int = 4, big_frac: float = 0.02):
+    """Pool index of each of ``count`` requests (small pool first, then big) and
+    the Poisson arrival offsets in units of the mean inter-arrival time."""
+    rng = np.random.default_rng(seed)
+    which = np.where(rng.random(count) < big_frac, n_small + rng.integers(0, n_big, count),
+                     rng.integers(0, n_small, count))
+    arrivals = np.cumsum(rng.exponential(1.0, count))
+    return which, arrivals
 
 
 def batch_mix_one(m: int, seed: int, n_lo: int = 500, n_hi: int = 20000) -> CSR:

@@ -21,8 +21,26 @@ def run_gpu(A, **opt):
     return r.to_host()
 
 
+def host_cores() -> int:
+    import os
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
 def oracle_full(A, nthreads=8):
     return oracle.full(A, nthreads=nthreads)
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_full_cached(key, A):
+    """oracle.full(A) on all host cores, kept for the session under `key` (the
+    batch and served tests compare the same seeded patterns)."""
+    r = _ORACLE_CACHE.get(key)
+    if r is None:
+        r = oracle.full(A, nthreads=host_cores())
+        _ORACLE_CACHE[key] = r
+    return r
 
 
 def assert_rows_equal(h, o, rows=None):

@@ -120,3 +120,86 @@ def test_space_budget_admission():
     assert st["completed"] == 7 and st["failed"] == 0
     assert st["peak_mem_in_use"] <= cap
     srv.close()
+
+
+def test_served_workload_every_result_exact():
+    """The served workload's pool (the 512-matrix mix and four 512^2 ND grids):
+    each distinct pattern run alone equals the oracle, and every result of a
+    stream of 1,500 requests through the benchmark's server shape (2 streams,
+    batches of up to 512, 150 GiB cap) equals its pattern run alone."""
+    import torch
+    import paper_2007_00840_gb300 as gs
+    from tests.gpu_util import oracle_full_cached
+    small, big = synth.served_pool()
+    pool = small + big
+    dev = [to_device(A) for A in pool]
+    alone = [gs.symbolic_device(rp, ci) for rp, ci in dev]
+    torch.cuda.synchronize()
+    hosts = gs.results_to_host(alone)
+    for k, (A, h) in enumerate(zip(pool, hosts)):
+        key = ("config", 3, k) if k < len(small) else ("served_big", k - len(small))
+        assert_same(h, oracle_full_cached(key, A)), k
+    del hosts
+    nreq = 1500
+    which, arrivals = synth.served_choices(nreq, len(small), len(big))
+    srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30)
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(nreq):
+        due = t0 + arrivals[i] * 0.0015  # about 670 requests/s
+        while time.perf_counter() < due:
+            pass
+        tickets.append(srv.submit(*dev[int(which[i])]))
+    bad = []
+    for i, t in enumerate(tickets):
+        r, _ = srv.wait(t)
+        a = alone[int(which[i])]
+        for f in FIELDS:
+            if not torch.equal(getattr(r, f), getattr(a, f)):
+                bad.append((i, int(which[i]), f))
+                break
+    st = srv.stats()
+    srv.close()
+    assert not bad, bad[:10]
+    assert st["completed"] == nreq and st["failed"] == 0
+    assert st["batches"] >= 2
+
+
+def test_served_malformed_request_fails_alone():
+    """A malformed pattern batched with valid ones fails with GSOFA_E_INVAL on its
+    own; every valid request of the same batch completes exactly as it would alone."""
+    import torch
+    import paper_2007_00840_gb300 as gs
+    pool = _pool()[:8]
+    dev = [to_device(A) for A in pool]
+    alone = [gs.symbolic_device(rp, ci).to_host() for rp, ci in dev]
+    torch.cuda.synchronize()
+    A = pool[2]
+    bad = A.colidx.copy()
+    bad[len(bad) // 2] = A.n + 11          # a column outside [0, n)
+    bad_dev = (dev[2][0], torch.from_numpy(bad).cuda())
+    srv = gs.Server(streams=1, max_batch=64)
+    # a large request first keeps the slot busy so the rest are batched together
+    tickets = [(srv.submit(*to_device(synth.grid2d_nd(200, 0.8, seed=3))), None)]
+    for i in range(24):
+        if i == 9:
+            tickets.append((srv.submit(*bad_dev), "bad"))
+        k = i % len(pool)
+        tickets.append((srv.submit(*dev[k]), k))
+    for t, k in tickets:
+        if k == "bad":
+            with pytest.raises(gs.GsofaError) as ei:
+                srv.wait(t)
+            assert ei.value.code == -1
+            continue
+        r, _ = srv.wait(t)
+        if k is None:
+            continue
+        h = r.to_host()
+        for f in FIELDS:
+            assert np.array_equal(getattr(h, f), getattr(alone[k], f)), (k, f)
+        if pool[k].n <= 5000:
+            assert_same(h, oracle_full(pool[k]))
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == len(tickets) - 1
+    srv.close()

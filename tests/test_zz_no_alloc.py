@@ -1,10 +1,10 @@
-"""The allocation-free sizing entry point, checked against the allocating one.
+"""The allocation-free sizing entry point, checked against the oracle.
 
 gsofa_row_counts_noalloc serves callers that cannot allocate device memory
 when they need the factor sizes (for example a solver that reserved the
 device's free memory up front, or a loop where cudaMalloc would synchronise
-the device).  It must give exactly the per-row sizes and fill counts that the
-regular entry point computes, call after call: its scratch array is shared and
+the device).  It must give exactly the per-row sizes and fill counts of the oracle
+(and so of the regular entry point), call after call: its scratch array is shared and
 keeps the previous call's contents, so two calls in a row are compared.
 This file is collected last so a failure here does not hide the other tests.
 """
@@ -13,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from tests.gpu_util import to_device
 
@@ -34,23 +35,29 @@ def _noalloc(lib, A, rp, ci):
     return nL[:n].cpu().numpy(), nU[:n].cpu().numpy(), fc[:n].cpu().numpy()
 
 
-@pytest.mark.parametrize("which", ["grid3d_32", "random_small", "banded"])
-def test_noalloc_counts_match_regular_entry_point(which):
-    import torch
+@pytest.mark.parametrize("which", ["grid3d_32", "random_small", "banded", "banded_max_n", "empty"])
+def test_noalloc_counts_match_oracle(which):
+    """Per-row sizes and fill counts equal the oracle's, on two calls in a row.
+    banded_max_n is the largest accepted order, where the frontier overflow lists
+    of a full grid of CTAs do not fit the fixed scratch and the launch uses fewer
+    CTAs; empty is n = 0."""
     import paper_2007_00840_gb300 as gs
+    from paper_2007_00840_gb300._lib import GSOFA_NOALLOC_MAX_N
     lib = gs.load()
     A = {"grid3d_32": lambda: synth.config(1),
          "random_small": lambda: synth.random_pattern(300, 0.02, seed=77, diag=False),
-         "banded": lambda: synth.banded(20000, 200, seed=5)}[which]()
+         "banded": lambda: synth.banded(20000, 200, seed=5),
+         "banded_max_n": lambda: synth.banded(GSOFA_NOALLOC_MAX_N, 300, seed=6),
+         "empty": lambda: synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), "empty")}[which]()
     rp, ci = to_device(A)
-    ref = gs.symbolic_device(rp, ci)
-    torch.cuda.synchronize()
-    h = ref.to_host()
-    want = (np.diff(h.L_rowptr).astype(np.int32), np.diff(h.U_rowptr).astype(np.int32), h.fill_count)
+    if A.n == 0:
+        ci = rp  # any valid device pointer; no column is read
+    o = oracle.symbolic(A, nthreads=16)
+    want = (o["nnzL"], o["nnzU"], oracle.fill_count(A, o["nnzL"], o["nnzU"]))
     for _ in range(2):  # the shared scratch keeps the previous call's contents
         got = _noalloc(lib, A, rp, ci)
         for g, w in zip(got, want):
-            assert np.array_equal(g, w)
+            assert np.array_equal(g, np.asarray(w, np.int32))
 
 
 def test_noalloc_rejects_oversize_and_bad_input():
