@@ -74,13 +74,13 @@ typedef struct gsofa_options {
                                     occupancy needs it; the rest spills to global memory) */
     int32_t max_ctas;            /* cap on traversal CTAs per launch, so concurrent launches share the GPU
                                     (default 0: one full wave) */
-    int32_t frontier_order;      /* 0: automatic; 1: breadth-first levels (shared-memory tier wherever the
-                                    maxId array fits on chip); 2: by increasing maxId class (warp tier).
-                                    Same result.  Automatic: when every source fits on chip, the first
-                                    call for a matrix (the same n and device buffers, or n and nnz for
-                                    host input) runs breadth-first and later calls switch to class
-                                    order if its frontiers averaged under 128 vertices per level;
-                                    with autotune = 1 both are timed once per shape instead */
+    int32_t frontier_order;      /* 0: automatic: class order for every source (sources below an explicit
+                                    smem_max_source stay breadth-first in shared memory); with
+                                    autotune = 1 both orders are timed once per (n, nnz) and the faster
+                                    kept.  1: breadth-first levels (shared-memory tier wherever the
+                                    maxId array fits on chip, class order above).  2: by increasing
+                                    maxId class for every source (visited bitmaps, one warp per
+                                    source).  Same result */
     int32_t label_bits;          /* shared-memory tier maxId width: 0 automatic (16 when n <= 65533), 16 or 32 */
     int32_t expand_mode;         /* shared-memory tier row access: 0 automatic, 1 CSR row slots per lane,
                                     2 CSR edge-balanced (a warp flattens its rows' entries), 3 16-byte
@@ -90,7 +90,11 @@ typedef struct gsofa_options {
                                     barrier each, 2 a worklist without level barriers (warps take
                                     queued vertices as they come; 16-bit labels and every vertex on
                                     chip only, else levels).  Same result */
-    int32_t reserved[2];
+    int32_t team_sources;        /* class-ordered kernel: how many of the largest sources a whole CTA of four
+                                    warps expands together (the rest: one warp each).  0 or -1: none (the
+                                    default: one warp per source was faster on every workload measured),
+                                    > 0: that many.  Same result */
+    int32_t reserved;
 } gsofa_options;
 
 /* Per-call statistics.  Times, cycles and edges_scanned are filled when

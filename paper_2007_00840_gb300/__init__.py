@@ -75,9 +75,10 @@ class DeviceResult:
     result and every tensor taken from it are gone).  Tensors are created on
     first access."""
 
-    def __init__(self, res: gsofa_result, stream: int):
+    def __init__(self, res: gsofa_result, stream: int, group=None):
         self._owner = _Owner(res)
         self._stream = stream
+        self._group = group  # results of one gsofa_batch call share one device block
         self._t = {}
         self.n = res.n
         self.nnz_L = int(res.nnz_L)
@@ -121,9 +122,10 @@ class DeviceResult:
 
 def results_to_host(results) -> list:
     """Copy device results to host arrays through pinned memory on the current
-    stream, with one synchronisation for all.  Arrays that are adjacent in device
-    memory (the results of one batch share one block per field) are copied as
-    one span, so a batch costs a few large copies instead of six per matrix."""
+    stream, with one synchronisation for all.  Arrays of one batch call that are
+    adjacent in device memory (its results share one block per field) are copied
+    as one span, so a batch costs a few large copies instead of six per matrix;
+    arrays of different calls are separate allocations and are copied apart."""
     import torch
     out = [[None] * len(_FIELDS) for _ in results]
     pending = []
@@ -134,15 +136,19 @@ def results_to_host(results) -> list:
             if count == 0:
                 out[k][f] = (torch.empty(0, dtype=dtype), 0, 0)
             else:
-                arrs.append((int(ptr), int(count), typestr, dtype, k))
+                # members of one batch call share a block (matrices above the on-chip
+                # limit, and empty ones, run alone and report their own traversal launches)
+                member = r._group is not None and r.n > 0 and r.stats.get("traverse_launches", 1) == 0
+                arrs.append((int(ptr), int(count), typestr, dtype, k, ("batch", r._group) if member else ("one", k)))
         arrs.sort(key=lambda x: x[0])
         i = 0
         while i < len(arrs):
-            ptr0, _, typestr, dtype, _ = arrs[i]
+            ptr0, _, typestr, dtype, _, _ = arrs[i]
             esz = 8 if typestr == "<i8" else 4
             end = ptr0 + arrs[i][1] * esz
             j = i + 1
-            while j < len(arrs) and arrs[j][2] == typestr and arrs[j][0] == end:
+            while (j < len(arrs) and arrs[j][2] == typestr and arrs[j][0] == end and arrs[j][5] == arrs[i][5]
+                   and arrs[i][5][0] == "batch"):
                 end += arrs[j][1] * esz
                 j += 1
             group = arrs[i:j]
@@ -274,10 +280,11 @@ def batch_device(mats, opts: gsofa_options | None = None, stream=None) -> list:
     if rc != 0:
         raise GsofaError(rc, -1, "gsofa_batch")
     res = []
+    group = object()
     for i in range(k):
         r = gsofa_result()
         ctypes.pointer(r)[0] = outs[i]
-        res.append(DeviceResult(r, sh))
+        res.append(DeviceResult(r, sh, group))
     return res
 
 

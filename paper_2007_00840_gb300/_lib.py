@@ -38,7 +38,8 @@ class gsofa_options(ctypes.Structure):
         ("label_bits", ctypes.c_int32),
         ("expand_mode", ctypes.c_int32),
         ("schedule", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("team_sources", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

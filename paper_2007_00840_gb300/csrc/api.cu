@@ -32,13 +32,12 @@ struct Ctx {
   int sms = 0;
   int smem_optin = 0;
   cudaMemPool_t mpool = nullptr;
-  // global-tier slots (persist across calls: the maxId windows live in them)
+  // slots of the class-ordered kernel (persist across calls; every source
+  // leaves its visited bitmap cleared)
   std::mutex gmu;
-  uint32_t* g_lab = nullptr;
-  int32_t* g_queue = nullptr;
-  int32_t* g_list = nullptr;
-  uint32_t* g_bits = nullptr;    // P | U bitmaps and their summaries, per slot
-  uint32_t* g_base = nullptr;
+  uint32_t* g_V = nullptr;       // visited bitmaps, cap/32 words per slot
+  uint32_t* g_VS = nullptr;      // their summaries, cap/1024 words per slot
+  int32_t* g_log = nullptr;      // level overflow and L row, cap per slot
   int64_t g_cap = 0;
   int g_slots = 0;
   cudaEvent_t g_done = nullptr;
@@ -49,8 +48,6 @@ struct Ctx {
   std::atomic<int64_t> free_bytes{-1};  // device memory free when first asked (slot sizing)
   // single-matrix autotune: faster frontier order by (n, nnz)
   std::map<std::pair<int32_t, int64_t>, int> order_tuned;
-  // single-matrix default: frontier order chosen from the first call's mean frontier size
-  std::map<std::pair<int32_t, int64_t>, int> order_learned;
 };
 
 std::mutex g_ctx_mu;
@@ -215,8 +212,9 @@ void note_pool_use(Ctx* c, unsigned long long used, long long rows) {
   if (r > c->rows_ratio) c->rows_ratio = r;
 }
 
-// Bytes of one global-tier slot of capacity cap (a multiple of 1024 vertices).
-int64_t slot_bytes(int64_t cap) { return cap * 16 + 2 * (cap / 8 + cap / 256); }
+// Bytes of one class-kernel slot of capacity cap (a multiple of 1024 vertices):
+// visited bitmap, its summary, and the log (level overflow and L row).
+int64_t slot_bytes(int64_t cap) { return cap / 8 + cap / 256 + 4 * cap; }
 
 // Memory for global-tier slots: half of the caller's budget, else half of the
 // device memory that is free or already held by slots, at most 96 GiB.
@@ -229,7 +227,7 @@ int64_t global_budget(const Ctx* c, const gsofa_options& o) {
   if (fr < 0) {
     size_t f = 0, tot = 0;
     if (cudaMemGetInfo(&f, &tot) == cudaSuccess) {
-      const int64_t held = c->g_lab ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
+      const int64_t held = c->g_V ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
       fr = (int64_t)f + held;
       int64_t expect = -1;
       const_cast<Ctx*>(c)->free_bytes.compare_exchange_strong(expect, fr);
@@ -242,49 +240,93 @@ int64_t global_budget(const Ctx* c, const gsofa_options& o) {
   return b;
 }
 
-// Slots (one warp each) of the global tier for order n: 32 per SM, within the
-// budget, at most 4 per CTA allowed by max_ctas.
+// Launch configuration of the class-ordered kernel for orders up to n_max.
+struct ClassCfg {
+  int sv = 0;            // visited bitmaps in shared memory
+  int warps_per_sm = 32; // register build (above 32: 48 registers)
+  int qw = 128;          // shared queue entries per warp and level parity
+  int vwords = 0;        // shared bitmap words per warp
+  int ctas_per_sm = 0;   // resident CTAs of four warps
+};
+
+ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
+  (void)c;
+  ClassCfg k;
+  k.warps_per_sm = warps_per_sm;
+  k.vwords = (n_max + 31) / 32;
+  const int want = warps_per_sm / CLASS_WARPS_PER_CTA;
+  const int occ_sv = trav_class_occupancy(1, warps_per_sm, k.vwords, k.qw);
+  // bitmaps on chip while that keeps at least 16 warps per SM
+  if (occ_sv >= 4) {
+    k.sv = 1;
+    k.ctas_per_sm = occ_sv < want ? occ_sv : want;
+  } else {
+    k.sv = 0;
+    const int occ = trav_class_occupancy(0, warps_per_sm, k.vwords, k.qw);
+    k.ctas_per_sm = occ < want ? occ : want;
+  }
+  return k;
+}
+
+// Slots (one warp each) of the class-ordered kernel for order n: a full wave
+// of resident warps, within the budget, at most 4 per CTA allowed by max_ctas.
 int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o) {
   const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
-  int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * 32;
+  const ClassCfg k = class_config(c, n, 32);
+  int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * k.ctas_per_sm * CLASS_WARPS_PER_CTA;
   const int64_t fit = global_budget(c, o) / slot_bytes(cap);
   if (slots > fit) slots = fit;
-  if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * GLOBAL_WARPS_PER_CTA)
-    slots = (int64_t)o.max_ctas * GLOBAL_WARPS_PER_CTA;
+  if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * CLASS_WARPS_PER_CTA)
+    slots = (int64_t)o.max_ctas * CLASS_WARPS_PER_CTA;
   return slots;
 }
 
-// Make sure the global-tier slots hold `slots` x `cap` vertices.  Caller holds gmu.
-int ensure_slots(Ctx* c, int64_t cap, int slots, cudaStream_t st) {
-  cap = (cap + 1023) / 1024 * 1024;
-  if (c->g_lab && c->g_cap >= cap && c->g_slots >= slots) return GSOFA_OK;
-  // the previous user of the slots must be done before they are replaced
-  cudaEventSynchronize(c->g_done);
-  cudaFree(c->g_lab);
-  cudaFree(c->g_queue);
-  cudaFree(c->g_list);
-  cudaFree(c->g_bits);
-  cudaFree(c->g_base);
-  c->g_lab = nullptr; c->g_queue = nullptr; c->g_list = nullptr; c->g_bits = nullptr; c->g_base = nullptr;
-  c->g_cap = 0; c->g_slots = 0;
-  const int64_t capW = cap / 32, capS = capW / 32;
-  const size_t bits_words = (size_t)(2 * capW + 2 * capS) * (size_t)slots;
-  if (cudaMalloc(&c->g_lab, sizeof(uint32_t) * cap * slots) != cudaSuccess ||
-      cudaMalloc(&c->g_queue, sizeof(int32_t) * 2 * cap * slots) != cudaSuccess ||
-      cudaMalloc(&c->g_list, sizeof(int32_t) * cap * slots) != cudaSuccess ||
-      cudaMalloc(&c->g_bits, sizeof(uint32_t) * bits_words) != cudaSuccess ||
-      cudaMalloc(&c->g_base, sizeof(uint32_t) * slots) != cudaSuccess) {
+// Allocate class-kernel slot arrays (zeroed bitmaps) for `slots` x `cap`
+// vertices; stream-ordered from the pool when `pool` is set, else cudaMalloc.
+int alloc_slot_arrays(Ctx* c, int64_t cap, int64_t slots, uint32_t** V, uint32_t** VS, int32_t** log, bool pool,
+                      cudaStream_t st) {
+  *V = nullptr; *VS = nullptr; *log = nullptr;
+  const size_t nV = (size_t)(cap / 32) * (size_t)slots, nVS = (size_t)(cap / 1024) * (size_t)slots;
+  const size_t nQ = (size_t)cap * (size_t)slots;
+  bool ok;
+  if (pool) {
+    ok = palloc(c, V, nV, st) == cudaSuccess && palloc(c, VS, nVS, st) == cudaSuccess &&
+         palloc(c, log, nQ, st) == cudaSuccess;
+  } else {
+    ok = cudaMalloc(V, 4 * nV) == cudaSuccess && cudaMalloc(VS, 4 * nVS) == cudaSuccess &&
+         cudaMalloc(log, 4 * nQ) == cudaSuccess;
+  }
+  if (!ok) {
     cudaGetLastError();
-    cudaFree(c->g_lab); cudaFree(c->g_queue); cudaFree(c->g_list); cudaFree(c->g_bits); cudaFree(c->g_base);
-    c->g_lab = nullptr; c->g_queue = nullptr; c->g_list = nullptr; c->g_bits = nullptr; c->g_base = nullptr;
+    for (void* q : {(void*)*V, (void*)*VS, (void*)*log})
+      if (q) { if (pool) cudaFreeAsync(q, st); else cudaFree(q); }
+    *V = nullptr; *VS = nullptr; *log = nullptr;
     return GSOFA_E_NOMEM;
   }
-  cudaMemsetAsync(c->g_lab, 0xFF, sizeof(uint32_t) * cap * slots, st);
-  cudaMemsetAsync(c->g_bits, 0, sizeof(uint32_t) * bits_words, st);
-  cudaMemsetAsync(c->g_base, 0xFF, sizeof(uint32_t) * slots, st);
+  if (cudaMemsetAsync(*V, 0, 4 * nV, st) != cudaSuccess || cudaMemsetAsync(*VS, 0, 4 * nVS, st) != cudaSuccess)
+    return GSOFA_E_CUDA;
+  return GSOFA_OK;
+}
+
+void free_slot_arrays(uint32_t*& V, uint32_t*& VS, int32_t*& log, bool pool, cudaStream_t st) {
+  for (void* q : {(void*)V, (void*)VS, (void*)log})
+    if (q) { if (pool) cudaFreeAsync(q, st); else cudaFree(q); }
+  V = nullptr; VS = nullptr; log = nullptr;
+}
+
+// Make sure the context's class-kernel slots hold `slots` x `cap` vertices.  Caller holds gmu.
+int ensure_slots(Ctx* c, int64_t cap, int slots, cudaStream_t st) {
+  cap = (cap + 1023) / 1024 * 1024;
+  if (c->g_V && c->g_cap >= cap && c->g_slots >= slots) return GSOFA_OK;
+  // the previous user of the slots must be done before they are replaced
+  cudaEventSynchronize(c->g_done);
+  free_slot_arrays(c->g_V, c->g_VS, c->g_log, false, st);
+  c->g_cap = 0; c->g_slots = 0;
+  const int rc = alloc_slot_arrays(c, cap, slots, &c->g_V, &c->g_VS, &c->g_log, false, st);
+  if (rc) return rc;
   c->g_cap = cap;
   c->g_slots = slots;
-  return cudaGetLastError() == cudaSuccess ? GSOFA_OK : GSOFA_E_CUDA;
+  return GSOFA_OK;
 }
 
 DevCounters* pinned_counters() {
@@ -328,6 +370,8 @@ struct Plan {
   int glob_block = 512;
   int glob_grid = 0;
   int async_sched = 0;    // shared tier: worklist schedule (the two lists form one ring >= S)
+  ClassCfg cls;           // class-ordered kernel (sources S .. n-1)
+  int32_t nbig = 0;       // of those, the largest expanded by four-warp CTA teams
 };
 
 }  // namespace
@@ -413,11 +457,15 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     if (o.max_ctas > 0 && o.max_ctas < p->smem_grid) p->smem_grid = o.max_ctas;
   }
   if (S < n) {
-    // one warp per source; as many warps as 32 per SM, within the memory budget
+    // one warp per source (the largest: a CTA); a full wave of warps within the memory budget
     const int64_t slots = global_slots(c, n, o);
     if (slots < 1) return GSOFA_E_NOMEM;
-    p->glob_block = 32 * GLOBAL_WARPS_PER_CTA;
+    p->cls = class_config(c, n, 32);
+    p->glob_block = 32 * CLASS_WARPS_PER_CTA;
     p->glob_grid = (int)slots;  // slots (warps); small CTAs spread any slot count over every SM
+    int64_t nbig = o.team_sources > 0 ? o.team_sources : 0;
+    if (nbig > n - S) nbig = n - S;
+    p->nbig = (int32_t)nbig;
   }
   return GSOFA_OK;
 }
@@ -447,6 +495,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->expand_mode = in->expand_mode;
   if (in->schedule < 0 || in->schedule > 2) return GSOFA_E_INVAL;
   o->schedule = in->schedule;
+  if (in->team_sources < -1) return GSOFA_E_INVAL;
+  o->team_sources = in->team_sources;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -570,21 +620,16 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.order = order + plan.S;
       a.nsrc = n - plan.S;
       a.ell = ell;
-      {
-        const int64_t capW = c->g_cap / 32, capS = capW / 32, slots = c->g_slots;
-        a.g_lab = c->g_lab;
-        a.g_queue = c->g_queue;
-        a.g_list = c->g_list;
-        a.g_P = c->g_bits;
-        a.g_U = c->g_bits + capW * slots;
-        a.g_PS = c->g_bits + 2 * capW * slots;
-        a.g_US = c->g_bits + 2 * capW * slots + capS * slots;
-        a.g_base = c->g_base;
-        a.g_cap = c->g_cap;
-        a.g_slots = plan.glob_grid;
-      }
-      LK(launch_trav_global(a, (plan.glob_grid + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
-                            plan.glob_block, st, 32));
+      a.g_V = c->g_V;
+      a.g_VS = c->g_VS;
+      a.g_log = c->g_log;
+      a.g_cap = c->g_cap;
+      a.g_slots = plan.glob_grid;
+      a.ct_qw = plan.cls.qw;
+      a.ct_vwords = plan.cls.vwords;
+      a.ct_nbig = plan.nbig;
+      LK(launch_trav_class(a, (plan.glob_grid + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, plan.cls.sv,
+                           plan.cls.warps_per_sm, st));
       CK(cudaEventRecord(c->g_done, st));
     }
     ev.rec(3, st);
@@ -750,14 +795,13 @@ struct BatchPlan {
   int64_t spill_cap = 0;
   int64_t spill_alloc = 0;
   int4* ell = nullptr;              // ELL records of every row (row_base + v)
-  // class-ordered tier slots (kernel 1)
-  uint32_t* c_lab = nullptr;
-  int32_t* c_queue = nullptr;
-  int32_t* c_list = nullptr;
-  uint32_t* c_bits = nullptr;
-  uint32_t* c_base = nullptr;
+  // class-ordered kernel slots (kernel 1)
+  uint32_t* c_V = nullptr;
+  uint32_t* c_VS = nullptr;
+  int32_t* c_log = nullptr;
   int64_t c_cap = 0;
   int c_slots = 0;
+  ClassCfg c_cfg;
   int grid = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -775,8 +819,8 @@ void free_plan(BatchPlan* p) {
   if (p->transient) {
     for (void* q : {(void*)p->d_mats, (void*)p->d_item_start, (void*)p->d_mat_order, (void*)p->d_ctr,
                     (void*)p->row_off, (void*)p->row_nL, (void*)p->row_nU, (void*)p->flags, (void*)p->fill,
-                    (void*)p->pool, (void*)p->spill, (void*)p->c_lab, (void*)p->c_queue, (void*)p->c_list,
-                    (void*)p->c_bits, (void*)p->c_base, (void*)p->ell})
+                    (void*)p->pool, (void*)p->spill, (void*)p->c_V, (void*)p->c_VS, (void*)p->c_log,
+                    (void*)p->ell})
       if (q) cudaFreeAsync(q, p->stream);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -797,11 +841,9 @@ void free_plan(BatchPlan* p) {
   cudaFree(p->fill);
   cudaFree(p->pool);
   cudaFree(p->spill);
-  cudaFree(p->c_lab);
-  cudaFree(p->c_queue);
-  cudaFree(p->c_list);
-  cudaFree(p->c_bits);
-  cudaFree(p->c_base);
+  cudaFree(p->c_V);
+  cudaFree(p->c_VS);
+  cudaFree(p->c_log);
   cudaFree(p->ell);
   if (p->h_ctr) cudaFreeHost(p->h_ctr);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -860,10 +902,12 @@ void save_tune_entry(uint64_t key, const LaunchShape& sh) {
   std::fclose(fp);
 }
 
-// Warps of the class-ordered tier for orders up to n_max: per_sm per SM, within 8 GiB.
+// Warps of the class-ordered kernel for orders up to n_max: per_sm per SM (as
+// far as the shared bitmaps allow), within 8 GiB.
 int class_slots(Ctx* c, int32_t n_max, int per_sm) {
   const int64_t cap = ((int64_t)n_max + 1023) / 1024 * 1024;
-  int64_t slots = (int64_t)c->sms * per_sm;
+  const ClassCfg k = class_config(c, n_max, per_sm);
+  int64_t slots = (int64_t)c->sms * k.ctas_per_sm * CLASS_WARPS_PER_CTA;
   const int64_t fit = ((int64_t)8 << 30) / slot_bytes(cap);
   if (slots > fit) slots = fit;
   return (int)slots;
@@ -939,19 +983,16 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   const unsigned rf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (t0 && (e = cudaEventRecordWithFlags(t0, st, rf)) != cudaSuccess) return e;
   if (p.shape.kernel == 1) {
-    const int64_t capW = p.c_cap / 32, capS = capW / 32, ns = p.c_slots;
-    a.g_lab = p.c_lab;
-    a.g_queue = p.c_queue;
-    a.g_list = p.c_list;
-    a.g_P = p.c_bits;
-    a.g_U = p.c_bits + capW * ns;
-    a.g_PS = p.c_bits + 2 * capW * ns;
-    a.g_US = p.c_bits + 2 * capW * ns + capS * ns;
-    a.g_base = p.c_base;
+    a.g_V = p.c_V;
+    a.g_VS = p.c_VS;
+    a.g_log = p.c_log;
     a.g_cap = p.c_cap;
     a.g_slots = p.shape.slots;
-    if ((e = launch_trav_global(a, (p.shape.slots + GLOBAL_WARPS_PER_CTA - 1) / GLOBAL_WARPS_PER_CTA,
-                                32 * GLOBAL_WARPS_PER_CTA, st, p.shape.occ)) != cudaSuccess)
+    a.ct_qw = p.c_cfg.qw;
+    a.ct_vwords = p.c_cfg.vwords;
+    a.ct_nbig = 0;
+    if ((e = launch_trav_class(a, (p.shape.slots + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, p.c_cfg.sv,
+                               p.c_cfg.warps_per_sm, st)) != cudaSuccess)
       return e;
   } else if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) {
     return e;
@@ -973,36 +1014,15 @@ int set_shape(Ctx* c, BatchPlan* p, const LaunchShape& sh) {
       p->gexec = nullptr;
     }
     const int64_t cap = ((int64_t)p->n_max + 1023) / 1024 * 1024;
-    if (p->c_lab && p->c_cap >= cap && p->c_slots >= sh.slots) return GSOFA_OK;
-    for (void* q : {(void*)p->c_lab, (void*)p->c_queue, (void*)p->c_list, (void*)p->c_bits, (void*)p->c_base})
-      if (q) { if (p->transient) cudaFreeAsync(q, p->stream); else cudaFree(q); }
-    p->c_lab = nullptr; p->c_queue = nullptr; p->c_list = nullptr; p->c_bits = nullptr; p->c_base = nullptr;
-    const int64_t ns = sh.slots, capW = cap / 32, capS = capW / 32;
-    const size_t bits_words = (size_t)(2 * capW + 2 * capS) * (size_t)ns;
+    p->c_cfg = class_config(c, p->n_max, sh.occ);
+    if (p->c_V && p->c_cap >= cap && p->c_slots >= sh.slots) return GSOFA_OK;
     cudaStream_t ast = p->transient ? p->stream : p->cap_stream;
-    bool ok;
-    if (p->transient) {
-      ok = palloc(c, &p->c_lab, (size_t)(cap * ns), ast) == cudaSuccess &&
-           palloc(c, &p->c_queue, (size_t)(2 * cap * ns), ast) == cudaSuccess &&
-           palloc(c, &p->c_list, (size_t)(cap * ns), ast) == cudaSuccess &&
-           palloc(c, &p->c_bits, bits_words, ast) == cudaSuccess && palloc(c, &p->c_base, (size_t)ns, ast) == cudaSuccess;
-    } else {
-      ok = cudaMalloc(&p->c_lab, sizeof(uint32_t) * (size_t)(cap * ns)) == cudaSuccess &&
-           cudaMalloc(&p->c_queue, sizeof(int32_t) * (size_t)(2 * cap * ns)) == cudaSuccess &&
-           cudaMalloc(&p->c_list, sizeof(int32_t) * (size_t)(cap * ns)) == cudaSuccess &&
-           cudaMalloc(&p->c_bits, sizeof(uint32_t) * bits_words) == cudaSuccess &&
-           cudaMalloc(&p->c_base, sizeof(uint32_t) * (size_t)ns) == cudaSuccess;
-    }
-    if (!ok) {
-      cudaGetLastError();
-      return GSOFA_E_NOMEM;
-    }
-    cudaMemsetAsync(p->c_lab, 0xFF, sizeof(uint32_t) * (size_t)(cap * ns), ast);
-    cudaMemsetAsync(p->c_bits, 0, sizeof(uint32_t) * bits_words, ast);
-    cudaMemsetAsync(p->c_base, 0xFF, sizeof(uint32_t) * (size_t)ns, ast);
+    free_slot_arrays(p->c_V, p->c_VS, p->c_log, p->transient, ast);
+    const int rc = alloc_slot_arrays(c, cap, sh.slots, &p->c_V, &p->c_VS, &p->c_log, p->transient, ast);
+    if (rc) return rc;
     if (!p->transient) cudaStreamSynchronize(ast);
     p->c_cap = cap;
-    p->c_slots = (int)ns;
+    p->c_slots = sh.slots;
     return GSOFA_OK;
   }
   // per CTA two overflow lists of (n_max - list capacity) entries
@@ -1362,7 +1382,7 @@ LaunchShape default_shape(Ctx* c, BatchCache& bc, const BatchPlan* p, const gsof
     sh.kernel = 1;
     sh.occ = 40;
     sh.slots = class_slots(c, p->n_max, 40);
-    if (o.max_ctas > 0 && sh.slots > o.max_ctas * GLOBAL_WARPS_PER_CTA) sh.slots = o.max_ctas * GLOBAL_WARPS_PER_CTA;
+    if (o.max_ctas > 0 && sh.slots > o.max_ctas * CLASS_WARPS_PER_CTA) sh.slots = o.max_ctas * CLASS_WARPS_PER_CTA;
     if (sh.slots > 0) { *rc = GSOFA_OK; return sh; }
     sh.kernel = 0;
   }
@@ -1611,14 +1631,17 @@ void gsofa_free(gsofa_result* res) {
 
 namespace {
 
-// One matrix: pick the frontier order (learned default or autotune), then run.
-// nnz < 0 (device input): the learned order is kept per (n, device buffers),
-// so no read is needed; autotune reads nnz and keeps its choice per (n, nnz).
+// One matrix: pick the frontier order (class order unless autotuned), then run.
+// Autotune reads nnz (device input: one read) and keeps its choice per (n, nnz).
 int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx, gsofa_options o,
                cudaStream_t st, gsofa_result* out, int64_t nnz_known) {
-  const bool learn = !o.autotune && o.frontier_order == 0 && o.smem_max_source == 0 && n > 0 &&
-                     n <= smem_tier_max_order();
   const bool tune = o.autotune && o.frontier_order == 0 && n > 0;
+  if (o.frontier_order == 0 && !tune) {
+    // class order for every source (the fewest expansions and the fastest on
+    // every workload measured); an explicit smem_max_source keeps the sources
+    // below it in the breadth-first shared-memory tier
+    o.frontier_order = o.smem_max_source > 0 ? 1 : 2;
+  }
   int64_t nnz = nnz_known;
   if (tune && nnz < 0) {
     int32_t v = 0;
@@ -1626,33 +1649,6 @@ int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
         wait_stream(st) != GSOFA_OK)
       return GSOFA_E_CUDA;
     nnz = v;
-  }
-  if (learn) {
-    // Every source fits the shared-memory tier.  Its breadth-first levels pay a
-    // barrier each, so when the first call of this shape found small frontiers
-    // (fewer than 128 vertices per level on average: long, thin searches such as
-    // 2D grids and banded patterns) later calls use the class-ordered warp tier.
-    const int64_t tag = nnz >= 0 ? nnz
-                                 : (int64_t)(mix64((uint64_t)(uintptr_t)d_rowptr, (uint64_t)(uintptr_t)d_colidx) |
-                                             (1ull << 62));
-    const std::pair<int32_t, int64_t> key(n, tag);
-    int learned = 0;
-    {
-      std::lock_guard<std::mutex> lk(c->hmu);
-      auto it = c->order_learned.find(key);
-      if (it != c->order_learned.end()) learned = it->second;
-    }
-    if (learned) {
-      o.frontier_order = learned;
-      return run_device(c, n, d_rowptr, d_colidx, o, st, out);
-    }
-    const int rc = run_device(c, n, d_rowptr, d_colidx, o, st, out);
-    if (rc == GSOFA_OK && out->stats.levels > 0) {
-      const double per_level = (double)out->stats.vertices_expanded / (double)out->stats.levels;
-      std::lock_guard<std::mutex> lk(c->hmu);
-      c->order_learned[key] = per_level < 128.0 ? 2 : 1;
-    }
-    return rc;
   }
   if (tune) {
     // time both frontier orders once for this shape and keep the faster

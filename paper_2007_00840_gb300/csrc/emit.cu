@@ -54,6 +54,7 @@ __global__ void init_counters_kernel(DevCounters* c) {
     c->n_super = 0;
     c->work_smem = 0;
     c->work_global = 0;
+    c->work_team = 0;
     c->levels = 0ull;
     c->cyc_trav = 0ull;
     c->cyc_emit = 0ull;

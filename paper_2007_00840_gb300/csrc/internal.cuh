@@ -20,9 +20,6 @@ enum : int32_t {
 
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-// Warps (= sources in flight) per CTA of the global-tier kernel: small CTAs so
-// that any slot count spreads over every SM.
-constexpr int GLOBAL_WARPS_PER_CTA = 4;
 
 // Counters in one small device block so one copy brings them back.
 struct DevCounters {
@@ -35,8 +32,9 @@ struct DevCounters {
   int32_t err_row;                  // first offending row (atomicMin), INT32_MAX if none
   int32_t n_super;                  // supernodes found
   int32_t work_smem;                // work counter of the shared-memory tier
-  int32_t work_global;              // work counter of the global tier
-  int32_t pad[3];
+  int32_t work_global;              // work counter of the global tier (class kernel: warp items)
+  int32_t work_team;                // class kernel: work counter of the CTA-team items
+  int32_t pad[2];
   unsigned long long levels;        // frontier levels over all sources (stats)
   unsigned long long cyc_trav;      // SM cycles in frontier levels (stats, thread 0 of each CTA)
   unsigned long long cyc_emit;      // SM cycles in row emission (stats)
@@ -90,18 +88,17 @@ struct TravArgs {
   int32_t nmats;
   int32_t chunk;                      // work items taken per fetch (>= 1)
   unsigned long long* mat_tot;        // per matrix: [sum nnz(L(i,:)), sum nnz(U(i,:))]
-  // global tier: per-slot working arrays (slot = warp)
-  uint32_t* g_lab;                    // slots x cap (epoch-encoded maxId)
-  int32_t* g_queue;                   // slots x 2cap (current / next class frontier)
-  int32_t* g_list;                    // slots x cap (the row's L columns, in order)
-  uint32_t* g_P;                      // slots x capW (pending fills, by id)
-  uint32_t* g_PS;                     // slots x capS (summary: bit per nonzero P word)
-  uint32_t* g_U;                      // slots x capW (U columns)
-  uint32_t* g_US;                     // slots x capS (summary of U)
-  uint32_t* g_base;                   // per slot: current maxId window base (persists across launches)
-  int64_t g_cap;                      // per-slot capacity in vertices (>= n, multiple of 1024)
-  int32_t g_slots;                    // number of slots (warps) of the launch
+  int64_t g_cap;                      // class kernel: per-slot capacity in vertices (>= n, multiple of 1024)
+  int32_t g_slots;                    // class kernel: number of slots (warps) of the launch
   int32_t async_sched;                // shared-memory tier: worklist without level barriers (16-bit, S >= n)
+  // class-ordered kernel (trav_class_kernel): per-slot visited bitmaps and
+  // logs; slot = warp of the launch, each g_cap vertices
+  uint32_t* g_V;                      // slots x g_cap/32 (global V only)
+  uint32_t* g_VS;                     // slots x g_cap/1024 (summary of g_V)
+  int32_t* g_log;                     // slots x g_cap (level overflow from the bottom, L row from the top)
+  int32_t ct_qw;                      // shared queue entries per warp and level parity
+  int32_t ct_vwords;                  // shared V: words per warp (>= ceil(n/32))
+  int32_t ct_nbig;                    // leading work items processed by four-warp CTA teams
 };
 
 // ---- launchers (return cudaGetLastError())
@@ -110,9 +107,12 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16);
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st);
 int trav_smem_static_bytes();
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16);
-// warps_per_sm: the slots per SM the launch was sized for (above 32: the
-// 48-register build of the kernel)
-cudaError_t launch_trav_global(const TravArgs& a, int grid, int block, cudaStream_t st, int warps_per_sm);
+// Class-ordered kernel with a visited bitmap (four-warp CTAs).  sv: V in shared
+// memory (ct_vwords words per warp); warps_per_sm above 32: 48-register build.
+cudaError_t launch_trav_class(const TravArgs& a, int grid, int sv, int warps_per_sm, cudaStream_t st);
+int trav_class_occupancy(int sv, int warps_per_sm, int vwords, int qw);
+size_t trav_class_smem(int sv, int vwords, int qw);
+constexpr int CLASS_WARPS_PER_CTA = 4;
 
 cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,
                             DevCounters* ctr, cudaStream_t st);

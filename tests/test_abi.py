@@ -57,7 +57,7 @@ int main(void) {
   printf("%zu %zu\n", offsetof(gsofa_stats, vertices_expanded), offsetof(gsofa_result, on_device));
   printf("%zu %zu %zu %zu\n", sizeof(gsofa_server_config), sizeof(gsofa_server_stats),
          offsetof(gsofa_server_config, opts), offsetof(gsofa_server_stats, span_s));
-  printf("%zu %zu %zu %zu\n", offsetof(gsofa_options, max_ctas), offsetof(gsofa_options, reserved),
+  printf("%zu %zu %zu %zu\n", offsetof(gsofa_options, max_ctas), offsetof(gsofa_options, team_sources),
          offsetof(gsofa_options, label_bits), offsetof(gsofa_options, schedule));
   return 0;
 }
@@ -74,7 +74,7 @@ int main(void) {
     assert vals[7:9] == [S.vertices_expanded.offset, R.on_device.offset]
     C, T = _lib.gsofa_server_config, _lib.gsofa_server_stats
     assert vals[9:13] == [ctypes.sizeof(C), ctypes.sizeof(T), C.opts.offset, T.span_s.offset]
-    assert vals[13:17] == [O.max_ctas.offset, O.reserved.offset, O.label_bits.offset, O.schedule.offset]
+    assert vals[13:17] == [O.max_ctas.offset, O.team_sources.offset, O.label_bits.offset, O.schedule.offset]
 
 
 def test_defaults_and_errors_without_gpu():
