@@ -94,7 +94,9 @@ typedef struct gsofa_options {
                                     warps expands together (the rest: one warp each).  0 or -1: none (the
                                     default: one warp per source was faster on every workload measured),
                                     > 0: that many.  Same result */
-    int32_t reserved;
+    int32_t warps_per_sm;        /* class-ordered kernel on one matrix: resident warps (sources in flight)
+                                    per SM, 0 automatic (32; 40 selects a 48-register build).  Batches
+                                    choose theirs with autotune */
 } gsofa_options;
 
 /* Per-call statistics.  Times, cycles and edges_scanned are filled when

@@ -39,7 +39,7 @@ class gsofa_options(ctypes.Structure):
         ("expand_mode", ctypes.c_int32),
         ("schedule", ctypes.c_int32),
         ("team_sources", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("warps_per_sm", ctypes.c_int32),
     ]
 
 

@@ -242,27 +242,32 @@ int64_t global_budget(const Ctx* c, const gsofa_options& o) {
 
 // Launch configuration of the class-ordered kernel for orders up to n_max.
 struct ClassCfg {
-  int sv = 0;            // visited bitmaps in shared memory
+  int vm = 0;            // where the visited bitmaps live: 0 shared memory, 1 global slots
   int warps_per_sm = 32; // register build (above 32: 48 registers)
   int qw = 128;          // shared queue entries per warp and level parity
-  int vwords = 0;        // shared bitmap words per warp
+  int vwords = 0;        // words of one visited bitmap (ceil(n_max / 32))
   int ctas_per_sm = 0;   // resident CTAs of four warps
 };
+
+constexpr int CLASS_VM_SMEM = 0, CLASS_VM_GLOBAL = 1;
 
 ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
   (void)c;
   ClassCfg k;
   k.warps_per_sm = warps_per_sm;
-  k.vwords = (n_max + 31) / 32;
   const int want = warps_per_sm / CLASS_WARPS_PER_CTA;
-  const int occ_sv = trav_class_occupancy(1, warps_per_sm, k.vwords, k.qw);
-  // bitmaps on chip while that keeps at least 16 warps per SM
+  const int words = (n_max + 31) / 32;
+  const int occ_sv = trav_class_occupancy(CLASS_VM_SMEM, warps_per_sm, words, k.qw);
   if (occ_sv >= 4) {
-    k.sv = 1;
+    // whole bitmaps on chip while that keeps at least 16 warps per SM
+    k.vm = CLASS_VM_SMEM;
+    k.vwords = words;
     k.ctas_per_sm = occ_sv < want ? occ_sv : want;
   } else {
-    k.sv = 0;
-    const int occ = trav_class_occupancy(0, warps_per_sm, k.vwords, k.qw);
+    // bitmaps in the global slots
+    k.vm = CLASS_VM_GLOBAL;
+    k.vwords = words;
+    const int occ = trav_class_occupancy(CLASS_VM_GLOBAL, warps_per_sm, k.vwords, k.qw);
     k.ctas_per_sm = occ < want ? occ : want;
   }
   return k;
@@ -272,7 +277,7 @@ ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
 // of resident warps, within the budget, at most 4 per CTA allowed by max_ctas.
 int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o) {
   const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
-  const ClassCfg k = class_config(c, n, 32);
+  const ClassCfg k = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
   int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * k.ctas_per_sm * CLASS_WARPS_PER_CTA;
   const int64_t fit = global_budget(c, o) / slot_bytes(cap);
   if (slots > fit) slots = fit;
@@ -460,7 +465,7 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     // one warp per source (the largest: a CTA); a full wave of warps within the memory budget
     const int64_t slots = global_slots(c, n, o);
     if (slots < 1) return GSOFA_E_NOMEM;
-    p->cls = class_config(c, n, 32);
+    p->cls = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
     p->glob_block = 32 * CLASS_WARPS_PER_CTA;
     p->glob_grid = (int)slots;  // slots (warps); small CTAs spread any slot count over every SM
     int64_t nbig = o.team_sources > 0 ? o.team_sources : 0;
@@ -497,6 +502,9 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->schedule = in->schedule;
   if (in->team_sources < -1) return GSOFA_E_INVAL;
   o->team_sources = in->team_sources;
+  if (in->warps_per_sm != 0 && (in->warps_per_sm < 4 || in->warps_per_sm > 48 || in->warps_per_sm % 4))
+    return GSOFA_E_INVAL;
+  o->warps_per_sm = in->warps_per_sm;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -628,7 +636,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.ct_qw = plan.cls.qw;
       a.ct_vwords = plan.cls.vwords;
       a.ct_nbig = plan.nbig;
-      LK(launch_trav_class(a, (plan.glob_grid + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, plan.cls.sv,
+      LK(launch_trav_class(a, (plan.glob_grid + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, plan.cls.vm,
                            plan.cls.warps_per_sm, st));
       CK(cudaEventRecord(c->g_done, st));
     }
@@ -991,7 +999,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
     a.ct_qw = p.c_cfg.qw;
     a.ct_vwords = p.c_cfg.vwords;
     a.ct_nbig = 0;
-    if ((e = launch_trav_class(a, (p.shape.slots + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, p.c_cfg.sv,
+    if ((e = launch_trav_class(a, (p.shape.slots + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, p.c_cfg.vm,
                                p.c_cfg.warps_per_sm, st)) != cudaSuccess)
       return e;
   } else if ((e = launch_trav_smem(a, p.grid, p.shape.block, p.label16, st)) != cudaSuccess) {
@@ -1430,6 +1438,7 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
   sig = mix64(sig, ((uint64_t)o.collect_stats << 32) ^ (uint64_t)o.max_ctas);
   sig = mix64(sig, ((uint64_t)o.frontier_order << 48) ^ ((uint64_t)o.expand_mode << 32) ^
                        ((uint64_t)o.label_bits << 16) ^ (uint64_t)o.autotune);
+  sig = mix64(sig, (uint64_t)(uint32_t)o.team_sources);
   std::unique_lock<std::mutex> lk(bc.mu);  // cached plans are used by one call at a time
   load_tune_file(bc);
   BatchPlan* p = nullptr;

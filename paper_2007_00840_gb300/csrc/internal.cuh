@@ -107,11 +107,12 @@ int32_t trav_smem_max_S(int32_t n, size_t smem_limit, int label16);
 cudaError_t launch_trav_smem(const TravArgs& a, int grid, int block, int label16, cudaStream_t st);
 int trav_smem_static_bytes();
 int trav_smem_occupancy(int block, size_t dyn_bytes, int label16);
-// Class-ordered kernel with a visited bitmap (four-warp CTAs).  sv: V in shared
-// memory (ct_vwords words per warp); warps_per_sm above 32: 48-register build.
-cudaError_t launch_trav_class(const TravArgs& a, int grid, int sv, int warps_per_sm, cudaStream_t st);
-int trav_class_occupancy(int sv, int warps_per_sm, int vwords, int qw);
-size_t trav_class_smem(int sv, int vwords, int qw);
+// Class-ordered kernel with a visited bitmap (four-warp CTAs).  vm: where the
+// bitmaps live (0 shared memory, ct_vwords words per warp; 1 global slots);
+// warps_per_sm above 32: 48-register build.
+cudaError_t launch_trav_class(const TravArgs& a, int grid, int vm, int warps_per_sm, cudaStream_t st);
+int trav_class_occupancy(int vm, int warps_per_sm, int vwords, int qw);
+size_t trav_class_smem(int vm, int vwords, int qw);
 constexpr int CLASS_WARPS_PER_CTA = 4;
 
 cudaError_t launch_validate(int32_t n, const int32_t* rowptr, const int32_t* colidx,

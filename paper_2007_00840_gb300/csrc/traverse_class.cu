@@ -25,17 +25,21 @@
 // sources of the issue order (the largest ones) the whole CTA of four warps,
 // whose levels of a class are split over 128 threads with one barrier per
 // level.  Persistent CTAs take team sources from one counter until they run
-// out, then each warp takes single sources from another.
+// out, then each warp takes single sources from another.  A level of q
+// vertices is expanded with 8, 4, 2 or 1 lanes per vertex (each lane relaxing
+// 1, 2, 4 or 8 of the vertex's record slots), chosen by q, so small levels
+// (class heads are single vertices) keep most lanes busy.
 //
-// Storage.  V is n bits per team: in shared memory (SV) when that leaves
-// enough CTAs per SM, else in a global-memory slot per warp with a summary
-// bitmap (one bit per nonzero V word) that bounds the searches and the
-// clearing.  Frontier levels live in shared-memory queues of `qw` entries per
-// warp; longer levels overflow into the slot's log array from its bottom, each
-// level after the previous one of the same class, while the L row grows down
-// from its top one class at a time (sorted by construction).  A vertex below s
-// is a class member or a fill, never both, and joins at most one level, so the
-// two ends never meet in s entries.  Each source clears the bits it set.
+// Where V lives (template parameter VM): VM_SMEM, all n bits in shared memory,
+// one bitmap per warp (orders whose bitmaps leave at least 16 warps per SM);
+// VM_GLOBAL, a global-memory slot per warp with a summary bitmap (one bit per
+// nonzero V word) that bounds the searches and the clearing.
+// Frontier levels live in shared-memory queues of `qw` entries per warp;
+// longer levels overflow into the slot's log array from its bottom, each level
+// after the previous one of the same class, while the L row grows down from
+// its top one class at a time (sorted by construction).  A vertex below s is a
+// class member or a fill, never both, and joins at most one level, so the two
+// ends never meet in s entries.  Each source clears the bits it set.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -48,33 +52,34 @@ namespace {
 
 constexpr int CT_WARPS = 4;  // warps per CTA (one team in team mode)
 constexpr int CT_THREADS = 32 * CT_WARPS;
+constexpr int VM_SMEM = 0, VM_GLOBAL = 1;
 
 // Per-team control block in shared memory.
 struct CtCtl {
-  int src;        // team mode: the current source (-1: no more team sources)
-  int mi;         // its matrix (batch mode)
+  int src;        // team mode: the current work item (-1: no more team items)
   int t;          // the class being expanded (-1: no pending class)
   int qcnt[3];    // rotating level lengths
   int smin, smax; // summary words touched (global V)
 };
 
-// ---- bit operations on V, in shared (SV) or global memory
+// ---- primitive bit operations
 // Atomic OR issued under a predicate; returns `bit` (= already set) when not issued.
-template <bool SV>
-__device__ __forceinline__ uint32_t v_or_if(uint32_t* V, int word, uint32_t bit, bool pred) {
+__device__ __forceinline__ uint32_t or_shared_if(uint32_t* p, uint32_t bit, bool pred) {
   uint32_t r = bit;
-  if constexpr (SV) {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(V + word);
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.or.b32 %0, [%1], %2;\n\t}"
-                 : "+r"(r)
-                 : "r"(a), "r"(bit), "r"((uint32_t)pred)
-                 : "memory");
-  } else {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.global.or.b32 %0, [%1], %2;\n\t}"
-                 : "+r"(r)
-                 : "l"(V + word), "r"(bit), "r"((uint32_t)pred)
-                 : "memory");
-  }
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.shared.or.b32 %0, [%1], %2;\n\t}"
+               : "+r"(r)
+               : "r"(a), "r"(bit), "r"((uint32_t)pred)
+               : "memory");
+  return r;
+}
+
+__device__ __forceinline__ uint32_t or_global_if(uint32_t* p, uint32_t bit, bool pred) {
+  uint32_t r = bit;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q atom.global.or.b32 %0, [%1], %2;\n\t}"
+               : "+r"(r)
+               : "l"(p), "r"(bit), "r"((uint32_t)pred)
+               : "memory");
   return r;
 }
 
@@ -82,38 +87,22 @@ __device__ __forceinline__ void red_or(uint32_t* p, uint32_t v) {
   asm volatile("red.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool SV>
-__device__ __forceinline__ uint32_t v_load(const uint32_t* V, int word) {
-  if constexpr (SV) return V[word];
-  else return *(const volatile uint32_t*)(V + word);
-}
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return *(const volatile uint32_t*)p; }
 
-// Set bit w of V (one lane).  Returns true when this call set it.  Global V:
-// a word that was empty gets its summary bit and widens [smin, smax].
-template <bool SV>
-__device__ __forceinline__ bool v_set(uint32_t* V, uint32_t* VS, int w, int& smin, int& smax) {
-  const uint32_t bit = 1u << (w & 31);
-  const uint32_t old = v_or_if<SV>(V, w >> 5, bit, true);
-  if (old & bit) return false;
-  if constexpr (!SV) {
-    if (old == 0u) {
-      red_or(VS + (w >> 10), 1u << ((w >> 5) & 31));
-      smin = min(smin, w >> 10);
-      smax = max(smax, w >> 10);
-    }
-  }
-  return true;
-}
-
-// The team's view of one source: where V, the queues and the list live.
+// The team's view of one source: where V, the queues and the log live.
 struct Team {
-  uint32_t* V;        // n bits
-  uint32_t* VS;       // summary (global V only)
+  uint32_t* V;        // VM_SMEM: n bits in shared memory; else the global slot (n bits)
+  uint32_t* VS;       // summary of the global slot
   int32_t* qa;        // shared queue, even levels
   int32_t* qb;        // shared queue, odd levels
   int qcap;           // shared queue capacity (entries per level)
   int32_t* log;       // level overflow from the bottom, L(s,:) from the top
   int64_t cap;        // entries of log (>= n)
+};
+
+// Per-lane bookkeeping of the global slot: the summary words touched.
+struct VState {
+  int smin, smax;
 };
 
 // Entry idx of the level with parity `level` whose overflow starts at log[base].
@@ -130,104 +119,123 @@ __device__ __forceinline__ int64_t next_base(const Team& tm, int64_t base, int q
   return base + (qlen > tm.qcap ? qlen - tm.qcap : 0);
 }
 
-// Smallest vertex of V in [from, s), or -1: the next pending class.
-// Warp-wide; every lane returns the same value.
-template <bool SV>
-__device__ int next_class(const Team& tm, int from, int s, int lane) {
-  if (from >= s) return -1;
+// Issue the OR of w's bit under pred.
+template <int VM>
+__device__ __forceinline__ uint32_t v_or_if(const Team& tm, int w, bool pred) {
+  const uint32_t bit = 1u << (w & 31);
+  if constexpr (VM == VM_SMEM) return or_shared_if(tm.V + (w >> 5), bit, pred);
+  else return or_global_if(tm.V + (w >> 5), bit, pred);
+}
+
+// Book-keeping after this lane's OR set w's bit first: a global word that was
+// empty gets its summary bit.
+template <int VM>
+__device__ __forceinline__ void v_first(const Team& tm, int w, uint32_t old, VState& st) {
+  if constexpr (VM == VM_GLOBAL) {
+    if (old == 0u) {
+      red_or(tm.VS + (w >> 10), 1u << ((w >> 5) & 31));
+      st.smin = min(st.smin, w >> 10);
+      st.smax = max(st.smax, w >> 10);
+    }
+  }
+}
+
+// Set bit w (one lane).  Returns true when this call set it.
+template <int VM>
+__device__ __forceinline__ bool v_set(const Team& tm, int w, VState& st) {
+  const uint32_t old = v_or_if<VM>(tm, w, true);
+  if (old & (1u << (w & 31))) return false;
+  v_first<VM>(tm, w, old, st);
+  return true;
+}
+
+// Smallest set bit at a vertex p in [from, lim) of a shared bitmap W whose
+// bit 0 is vertex `base` (base a multiple of 32); -1 if none.  Warp-wide.
+__device__ int scan_smem(const uint32_t* W, int base, int from, int lim, int lane) {
+  if (from >= lim) return -1;
+  const int wfirst = (from - base) >> 5;
+  const int wend = (lim - base + 31) >> 5;
+  for (int w0 = wfirst; w0 < wend; w0 += 32) {
+    const int j = w0 + lane;
+    uint32_t m = 0u;
+    if (j < wend) {
+      m = W[j];
+      if (j == wfirst) m &= 0xFFFFFFFFu << ((from - base) & 31);
+      const int hi = lim - base - (j << 5);
+      if (hi < 32) m &= (1u << hi) - 1u;
+    }
+    const unsigned b = __ballot_sync(FULL, m != 0u);
+    if (b) {
+      const int l = __ffs(b) - 1;
+      m = __shfl_sync(FULL, m, l);
+      return base + ((w0 + l) << 5) + __ffs(m) - 1;
+    }
+  }
+  return -1;
+}
+
+// Smallest set bit in [from, lim) of the global slot, through its summary; -1
+// if none.  Warp-wide.
+__device__ int scan_global(const Team& tm, int from, int lim, int lane) {
+  if (from >= lim) return -1;
   const int wfirst = from >> 5;
-  const int wend = (s + 31) >> 5;  // words holding positions below s
-  if constexpr (SV) {
-    for (int w0 = wfirst; w0 < wend; w0 += 32) {
-      const int j = w0 + lane;
-      uint32_t m = 0u;
-      if (j < wend) {
-        m = v_load<SV>(tm.V, j);
-        if (j == wfirst) m &= 0xFFFFFFFFu << (from & 31);
-        const int hi = s - (j << 5);
-        if (hi < 32) m &= (1u << hi) - 1u;
-      }
-      const unsigned b = __ballot_sync(FULL, m != 0u);
-      if (b) {
-        const int l = __ffs(b) - 1;
-        m = __shfl_sync(FULL, m, l);
-        return ((w0 + l) << 5) + __ffs(m) - 1;
-      }
-    }
-    return -1;
-  } else {
-    // the cursor's own word first
-    uint32_t m = v_load<SV>(tm.V, wfirst) & (0xFFFFFFFFu << (from & 31));
-    if (m) {
-      const int v = (wfirst << 5) + __ffs(m) - 1;
-      return v < s ? v : -1;
-    }
-    // then the summary from the next word on
-    const int wstart = wfirst + 1;
-    if (wstart >= wend) return -1;
-    const int send = (wend + 31) >> 5;
-    for (int sw0 = wstart >> 5; sw0 < send; sw0 += 32) {
-      const int sw = sw0 + lane;
-      uint32_t sm = 0u;
-      if (sw < send) {
-        sm = v_load<SV>(tm.VS, sw);
-        if (sw == (wstart >> 5)) sm &= 0xFFFFFFFFu << (wstart & 31);
-      }
-      const unsigned b = __ballot_sync(FULL, sm != 0u);
-      if (b) {
-        const int l = __ffs(b) - 1;
-        sm = __shfl_sync(FULL, sm, l);
-        const int pw = ((sw0 + l) << 5) + __ffs(sm) - 1;  // first nonzero V word at or after wstart
-        const uint32_t word = v_load<SV>(tm.V, pw);
-        const int v = (pw << 5) + __ffs(word) - 1;
-        return (word != 0u && v < s) ? v : -1;
-      }
-    }
-    return -1;
+  const int wend = (lim + 31) >> 5;
+  // the cursor's own word first
+  const uint32_t m = ld_cg(tm.V + wfirst) & (0xFFFFFFFFu << (from & 31));
+  if (m) {
+    const int v = (wfirst << 5) + __ffs(m) - 1;
+    return v < lim ? v : -1;
   }
+  // then the summary from the next word on
+  const int wstart = wfirst + 1;
+  if (wstart >= wend) return -1;
+  const int send = (wend + 31) >> 5;
+  for (int sw0 = wstart >> 5; sw0 < send; sw0 += 32) {
+    const int sw = sw0 + lane;
+    uint32_t sm = 0u;
+    if (sw < send) {
+      sm = ld_cg(tm.VS + sw);
+      if (sw == (wstart >> 5)) sm &= 0xFFFFFFFFu << (wstart & 31);
+    }
+    const unsigned b = __ballot_sync(FULL, sm != 0u);
+    if (b) {
+      const int l = __ffs(b) - 1;
+      sm = __shfl_sync(FULL, sm, l);
+      const int pw = ((sw0 + l) << 5) + __ffs(sm) - 1;  // first nonzero word at or after wstart
+      const uint32_t word = ld_cg(tm.V + pw);
+      const int v = (pw << 5) + __ffs(word) - 1;
+      return (word != 0u && v < lim) ? v : -1;
+    }
+  }
+  return -1;
 }
 
-// Relax the 8 record slots of vertex v for class t of source s.  The OR
-// operations are issued together (predicated), then the first-reached
-// vertices below t are returned as a slot mask (members of class t).
-template <bool SV>
-__device__ __forceinline__ unsigned relax8(const Team& tm, const int (&wv)[8], int v, int s, int t, int& smin,
-                                           int& smax) {
-  uint32_t old[8];
-#pragma unroll
-  for (int q = 0; q < 8; q++) {
-    const int w = wv[q];
-    old[q] = v_or_if<SV>(tm.V, (w < 0 ? 0 : w) >> 5, 1u << (w & 31), w != v && w != s);
-  }
-  unsigned em = 0u;
-#pragma unroll
-  for (int q = 0; q < 8; q++) {
-    const int w = wv[q];
-    const uint32_t bit = 1u << (w & 31);
-    if (!(old[q] & bit)) {  // first reach (not issued: old == bit)
-      if constexpr (!SV) {
-        if (old[q] == 0u) {
-          red_or(tm.VS + (w >> 10), 1u << ((w >> 5) & 31));
-          smin = min(smin, w >> 10);
-          smax = max(smax, w >> 10);
-        }
-      }
-      if (w < t) em |= 1u << q;
-    }
-  }
-  return em;
+// Smallest vertex of V in [from, s): the next pending class, or -1.
+template <int VM>
+__device__ int next_class(const Team& tm, int from, int s, int lane) {
+  if constexpr (VM == VM_SMEM) return scan_smem(tm.V, 0, from, s, lane);
+  else return scan_global(tm, from, s, lane);
 }
 
-// Decode an ELL record of v into its neighbours (empty slots hold v itself).
-__device__ __forceinline__ void decode(const int4 r4, int v, int (&wv)[8], bool& fallback) {
-  uint32_t h0 = (uint32_t)r4.x;
-  fallback = (h0 & 0xFFFFu) == 0x8000u;
-  if (fallback) h0 = 0u;
-  const uint32_t h1 = (uint32_t)r4.y, h2 = (uint32_t)r4.z, h3 = (uint32_t)r4.w;
-  wv[0] = v + (int)(short)(h0 & 0xFFFFu); wv[1] = v + (int)(short)(h0 >> 16);
-  wv[2] = v + (int)(short)(h1 & 0xFFFFu); wv[3] = v + (int)(short)(h1 >> 16);
-  wv[4] = v + (int)(short)(h2 & 0xFFFFu); wv[5] = v + (int)(short)(h2 >> 16);
-  wv[6] = v + (int)(short)(h3 & 0xFFFFu); wv[7] = v + (int)(short)(h3 >> 16);
+// Relax slots [Q0, Q0 + G) of the lane's record group (their OR operations
+// issued together); first-reached vertices below t set their bit in em.
+template <int VM, int K, int Q0, int G>
+__device__ __forceinline__ void relax_group(const Team& tm, const int (&wv)[K], int v, int s, int t, unsigned& em,
+                                            VState& st) {
+  uint32_t old[G];
+#pragma unroll
+  for (int q = 0; q < G; q++) {
+    const int w = wv[Q0 + q];
+    old[q] = v_or_if<VM>(tm, w, w != v && w != s);
+  }
+#pragma unroll
+  for (int q = 0; q < G; q++) {
+    const int w = wv[Q0 + q];
+    if (!(old[q] & (1u << (w & 31)))) {  // first reach (an OR not issued returns the bit)
+      v_first<VM>(tm, w, old[q], st);
+      if (w < t) em |= 1u << (Q0 + q);
+    }
+  }
 }
 
 // Source-independent inputs of one source.
@@ -245,12 +253,28 @@ struct Src {
 
 namespace {
 
+// Append this warp's `cnt` new entries (in lane order) to the next level:
+// warp mode bumps nq, team mode takes room from the shared counter.  Returns
+// the level index of the warp's first entry.
+template <bool TEAM>
+__device__ __forceinline__ int append_base(CtCtl* ctl, int level, int tot, int& nq) {
+  if constexpr (TEAM) {
+    int base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(&ctl->qcnt[(level + 1) % 3], tot);
+    return __shfl_sync(FULL, base, 0);
+  } else {
+    const int base = nq;
+    nq += tot;
+    return base;
+  }
+}
+
 // Walk row u from the CSR (rows without an ELL record, or no records at all):
 // the warp takes 32 entries at a time; first-reached vertices below t join the
 // next level.  Columns are range-checked here.
-template <bool SV, bool TEAM>
+template <int VM, bool TEAM>
 __device__ void walk_row(const Src& sc, const Team& tm, CtCtl* ctl, int u, int t, int level, int64_t nb, int& nq,
-                         int& smin, int& smax, int& bad) {
+                         VState& st, int& bad) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int eb = __ldg(sc.rowptr + u), ee = __ldg(sc.rowptr + u + 1);
@@ -263,129 +287,33 @@ __device__ void walk_row(const Src& sc, const Team& tm, CtCtl* ctl, int u, int t
       if ((unsigned)w >= (unsigned)sc.n) {
         bad = 1;
       } else if (w != u && w != sc.s) {
-        enq = v_set<SV>(tm.V, tm.VS, w, smin, smax) && w < t;
+        enq = v_set<VM>(tm, w, st) && w < t;
       }
     }
     const unsigned m = __ballot_sync(FULL, enq);
     if (!m) continue;
-    int base;
-    if constexpr (TEAM) {
-      if (lane == 0) base = atomicAdd(&ctl->qcnt[(level + 1) % 3], __popc(m));
-      base = __shfl_sync(FULL, base, 0);
-    } else {
-      base = nq;
-      nq += __popc(m);
-    }
+    const int base = append_base<TEAM>(ctl, level, __popc(m), nq);
     if (enq) *q_slot(tm, level + 1, nb, base + __popc(m & lt)) = w;
   }
 }
 
-// Expand one level of class t: the calling warp (TEAM false) or the whole CTA
-// (TEAM true) takes the level's vertices, relaxes their neighbours and appends
-// the first-reached vertices below t to the next level.  head: the class's
-// first level, t alone (qlen 1).  `level` indexes the queues and counters.
-// Warp mode returns the next level's length in nq; team mode counts it in
-// ctl->qcnt[(level + 1) % 3].
-template <bool SV, bool TEAM>
+// One level of class t with LPV lanes per vertex: the calling warp (TEAM
+// false) or the CTA (TEAM true) takes the level's vertices, each lane relaxing
+// K = 8/LPV consecutive record slots of its vertex, and appends the
+// first-reached vertices below t to the next level.  head: the class's first
+// level, t alone.  `level` indexes the queues (parity) and team counters; the
+// level's overflow starts at log[cb], the next level's at log[nb].
+template <int VM, bool TEAM, int LPV>
 __device__ void expand_level(const TravArgs& a, const Src& sc, const Team& tm, CtCtl* ctl, int t, int level,
-                             int64_t cb, int64_t nb, bool head, int qlen, int& nq, int& smin, int& smax,
+                             int64_t cb, int64_t nb, bool head, int qlen, int& nq, VState& st,
                              unsigned long long& n_exp, unsigned long long& n_edge, int& bad) {
-  const int lane = threadIdx.x & 31;
-  const int nthr = TEAM ? CT_THREADS : 32;
-  const int tid = TEAM ? (int)threadIdx.x : lane;
-  for (int i0 = 0; i0 < qlen; i0 += nthr) {
-    const int i = i0 + tid;
-    int v = -1;
-    if (i < qlen) v = head ? t : *q_slot(tm, level, cb, i);
-    int wv[8];
-    bool fb = false;
-    unsigned em = 0u;
-    if (v >= 0) {
-      if (sc.ell) {
-        decode(__ldg(sc.ell + v), v, wv, fb);
-        if (!fb) em = relax8<SV>(tm, wv, v, sc.s, t, smin, smax);
-      } else {
-        fb = true;
-      }
-      if (a.collect_stats) {
-        n_exp++;
-        n_edge += (unsigned long long)(__ldg(sc.rowptr + v + 1) - __ldg(sc.rowptr + v));
-      }
-    }
-    // append the members found through records
-    const int cnt = __popc(em);
-    int inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int x = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += x;
-    }
-    const int tot = __shfl_sync(FULL, inc, 31);
-    if (tot) {
-      int base;
-      if constexpr (TEAM) {
-        if (lane == 0) base = atomicAdd(&ctl->qcnt[(level + 1) % 3], tot);
-        base = __shfl_sync(FULL, base, 0);
-      } else {
-        base = nq;
-        nq += tot;
-      }
-      int pos = base + inc - cnt;
-#pragma unroll
-      for (int q = 0; q < 8; q++)
-        if ((em >> q) & 1u) *q_slot(tm, level + 1, nb, pos++) = wv[q];
-    }
-    // rows read from the CSR
-    unsigned fm = __ballot_sync(FULL, fb);
-    while (fm) {
-      const int l = __ffs(fm) - 1;
-      fm &= fm - 1;
-      walk_row<SV, TEAM>(sc, tm, ctl, __shfl_sync(FULL, v, l), t, level, nb, nq, smin, smax, bad);
-    }
-  }
-}
-
-// Relax slots [Q0, Q0 + G) of the lane's K-slot group (their OR operations
-// issued together); first-reached vertices below t set their bit in em.
-template <bool SV, int K, int Q0, int G>
-__device__ __forceinline__ void relax_group(const Team& tm, const int (&wv)[K], int v, int s, int t, unsigned& em,
-                                            int& smin, int& smax) {
-  uint32_t old[G];
-#pragma unroll
-  for (int q = 0; q < G; q++) {
-    const int w = wv[Q0 + q];
-    old[q] = v_or_if<SV>(tm.V, w >> 5, 1u << (w & 31), w != v && w != s);
-  }
-#pragma unroll
-  for (int q = 0; q < G; q++) {
-    const int w = wv[Q0 + q];
-    if (!(old[q] & (1u << (w & 31)))) {  // first reach (an OR not issued returns the bit)
-      if constexpr (!SV) {
-        if (old[q] == 0u) {
-          red_or(tm.VS + (w >> 10), 1u << ((w >> 5) & 31));
-          smin = min(smin, w >> 10);
-          smax = max(smax, w >> 10);
-        }
-      }
-      if (w < t) em |= 1u << (Q0 + q);
-    }
-  }
-}
-
-// Warp mode: one level with LPV lanes per vertex, each lane relaxing K = 8/LPV
-// consecutive record slots of its vertex (small levels keep most lanes busy:
-// a class head alone takes one round of 8 lanes instead of one lane doing 8
-// slots).  Appends members to the next level (length in nq).
-template <bool SV, int LPV>
-__device__ void expand_level_warp(const TravArgs& a, const Src& sc, const Team& tm, int t, int level, int64_t cb,
-                                  int64_t nb, bool head, int qlen, int& nq, int& smin, int& smax,
-                                  unsigned long long& n_exp, unsigned long long& n_edge, int& bad) {
   constexpr int K = 8 / LPV;
-  constexpr int PER = 32 / LPV;  // vertices per round
+  constexpr int PER = (TEAM ? CT_THREADS : 32) / LPV;  // vertices per round
   const int lane = threadIdx.x & 31;
+  const int rank = TEAM ? (int)threadIdx.x : lane;
   const unsigned lt = (1u << lane) - 1u;
-  const int sub = lane % LPV;    // which K slots of the vertex
-  const int vi = lane / LPV;
+  const int sub = lane % LPV;  // which K slots of the vertex
+  const int vi = rank / LPV;
   for (int i0 = 0; i0 < qlen; i0 += PER) {
     const int i = i0 + vi;
     int v = -1;
@@ -428,20 +356,23 @@ __device__ void expand_level_warp(const TravArgs& a, const Src& sc, const Team& 
     }
     if constexpr (K == 8) {
       // records are packed, so slots 4-7 are empty for rows of up to 4 neighbours
-      relax_group<SV, 8, 0, 4>(tm, wv, vv, sc.s, t, em, smin, smax);
-      if (__any_sync(FULL, (h[2] | h[3]) != 0u)) relax_group<SV, 8, 4, 4>(tm, wv, vv, sc.s, t, em, smin, smax);
+      relax_group<VM, 8, 0, 4>(tm, wv, vv, sc.s, t, em, st);
+      if (__any_sync(FULL, (h[2] | h[3]) != 0u)) relax_group<VM, 8, 4, 4>(tm, wv, vv, sc.s, t, em, st);
     } else {
-      relax_group<SV, K, 0, K>(tm, wv, vv, sc.s, t, em, smin, smax);
+      relax_group<VM, K, 0, K>(tm, wv, vv, sc.s, t, em, st);
     }
     // append the members: ballots for one or two slots per lane, else a scan
     if constexpr (K <= 2) {
       const unsigned b0 = __ballot_sync(FULL, em & 1u);
       unsigned b1 = 0u;
       if constexpr (K == 2) b1 = __ballot_sync(FULL, em & 2u);
-      if (em & 1u) *q_slot(tm, level + 1, nb, nq + __popc(b0 & lt)) = wv[0];
-      if constexpr (K == 2)
-        if (em & 2u) *q_slot(tm, level + 1, nb, nq + __popc(b0) + __popc(b1 & lt)) = wv[1];
-      nq += __popc(b0) + __popc(b1);
+      const int tot = __popc(b0) + __popc(b1);
+      if (tot) {
+        const int base = append_base<TEAM>(ctl, level, tot, nq);
+        if (em & 1u) *q_slot(tm, level + 1, nb, base + __popc(b0 & lt)) = wv[0];
+        if constexpr (K == 2)
+          if (em & 2u) *q_slot(tm, level + 1, nb, base + __popc(b0) + __popc(b1 & lt)) = wv[1];
+      }
     } else {
       const int cnt = __popc(em);
       int inc = cnt;
@@ -452,81 +383,143 @@ __device__ void expand_level_warp(const TravArgs& a, const Src& sc, const Team& 
       }
       const int tot = __shfl_sync(FULL, inc, 31);
       if (tot) {
-        int pos = nq + inc - cnt;
+        int pos = append_base<TEAM>(ctl, level, tot, nq) + inc - cnt;
 #pragma unroll
         for (int q = 0; q < K; q++)
           if ((em >> q) & 1u) *q_slot(tm, level + 1, nb, pos++) = wv[q];
-        nq += tot;
       }
     }
     unsigned fm = __ballot_sync(FULL, fb);
     while (fm) {
       const int l = __ffs(fm) - 1;
       fm &= fm - 1;
-      walk_row<SV, false>(sc, tm, nullptr, __shfl_sync(FULL, v, l), t, level, nb, nq, smin, smax, bad);
+      walk_row<VM, TEAM>(sc, tm, ctl, __shfl_sync(FULL, v, l), t, level, nb, nq, st, bad);
     }
   }
 }
 
-// Warp mode: pick the lanes per vertex from the level's length.
-template <bool SV>
-__device__ __forceinline__ void expand_warp(const TravArgs& a, const Src& sc, const Team& tm, int t, int level,
-                                            int64_t cb, int64_t nb, bool head, int qlen, int& nq, int& smin,
-                                            int& smax, unsigned long long& n_exp, unsigned long long& n_edge,
-                                            int& bad) {
-  if (qlen <= 4)
-    expand_level_warp<SV, 8>(a, sc, tm, t, level, cb, nb, head, qlen, nq, smin, smax, n_exp, n_edge, bad);
-  else if (qlen <= 8)
-    expand_level_warp<SV, 4>(a, sc, tm, t, level, cb, nb, head, qlen, nq, smin, smax, n_exp, n_edge, bad);
-  else if (qlen <= 16)
-    expand_level_warp<SV, 2>(a, sc, tm, t, level, cb, nb, head, qlen, nq, smin, smax, n_exp, n_edge, bad);
+// Lanes per vertex from the level's length: a warp covers 32/LPV vertices per
+// round (a team four times as many).
+template <int VM, bool TEAM>
+__device__ __forceinline__ void expand(const TravArgs& a, const Src& sc, const Team& tm, CtCtl* ctl, int t,
+                                       int level, int64_t cb, int64_t nb, bool head, int qlen, int& nq, VState& st,
+                                       unsigned long long& n_exp, unsigned long long& n_edge, int& bad) {
+  constexpr int R = TEAM ? CT_WARPS : 1;
+  if (qlen <= 4 * R)
+    expand_level<VM, TEAM, 8>(a, sc, tm, ctl, t, level, cb, nb, head, qlen, nq, st, n_exp, n_edge, bad);
+  else if (qlen <= 8 * R)
+    expand_level<VM, TEAM, 4>(a, sc, tm, ctl, t, level, cb, nb, head, qlen, nq, st, n_exp, n_edge, bad);
+  else if (qlen <= 16 * R)
+    expand_level<VM, TEAM, 2>(a, sc, tm, ctl, t, level, cb, nb, head, qlen, nq, st, n_exp, n_edge, bad);
   else
-    expand_level_warp<SV, 1>(a, sc, tm, t, level, cb, nb, head, qlen, nq, smin, smax, n_exp, n_edge, bad);
+    expand_level<VM, TEAM, 1>(a, sc, tm, ctl, t, level, cb, nb, head, qlen, nq, st, n_exp, n_edge, bad);
+}
+
+}  // namespace
+
+namespace {
+
+__device__ __forceinline__ int warp_sum(int x) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+__device__ __forceinline__ int warp_min(int x) { return __reduce_min_sync(FULL, x); }
+__device__ __forceinline__ int warp_max(int x) { return __reduce_max_sync(FULL, x); }
+
+// Set bits of shared words [j0, j1) (word j0 masked by m0).  Warp-wide count.
+__device__ int count_smem(const uint32_t* W, int j0, int j1, uint32_t m0, int lane) {
+  int c = 0;
+  for (int jb = j0; jb < j1; jb += 32) {
+    const int j = jb + lane;
+    uint32_t m = j < j1 ? W[j] : 0u;
+    if (j == j0) m &= m0;
+    c += __popc(m);
+  }
+  return warp_sum(c);
+}
+
+// Write, in increasing order from pool[pos], the vertices of the set bits of
+// shared words [j0, j1) (word j0 masked by m0; word 0 is vertex base).
+__device__ long long write_smem(const uint32_t* W, int base, int j0, int j1, uint32_t m0, uint32_t* pool,
+                                long long pos, int lane) {
+  for (int jb = j0; jb < j1; jb += 32) {
+    const int j = jb + lane;
+    uint32_t word = j < j1 ? W[j] : 0u;
+    if (j == j0) word &= m0;
+    const int c = __popc(word);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += x;
+    }
+    long long p = pos + (inc - c);
+    while (word) {
+      const int b = __ffs(word) - 1;
+      word &= word - 1;
+      pool[p++] = (uint32_t)(base + (j << 5) + b);
+    }
+    pos += __shfl_sync(FULL, inc, 31);
+  }
+  return pos;
+}
+
+// Set bits of the global slot from word ws on (ws masked by m0), through the
+// summary up to summary word swmax.  count: returns the number; else writes
+// them in increasing order from pool[pos] and returns the end position.
+template <bool COUNT>
+__device__ long long scan_global_words(const Team& tm, int ws, uint32_t m0, int swmax, uint32_t* pool,
+                                       long long pos, int lane) {
+  long long c = 0;
+  for (int sw0 = ws >> 5; sw0 <= swmax; sw0 += 32) {
+    const int sw = sw0 + lane;
+    uint32_t sm = sw <= swmax ? ld_cg(tm.VS + sw) : 0u;
+    if (sw == (ws >> 5)) sm &= 0xFFFFFFFFu << (ws & 31);
+    unsigned any = __ballot_sync(FULL, sm != 0u);
+    while (any) {
+      const int l = __ffs(any) - 1;
+      any &= any - 1;
+      const uint32_t ml = __shfl_sync(FULL, sm, l);
+      const int pw = ((sw0 + l) << 5) + lane;
+      uint32_t word = ((ml >> lane) & 1u) ? ld_cg(tm.V + pw) : 0u;
+      if (pw == ws) word &= m0;
+      const int cw = __popc(word);
+      if constexpr (COUNT) {
+        c += warp_sum(cw);
+      } else {
+        int inc = cw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int x = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += x;
+        }
+        long long p = pos + (inc - cw);
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          pool[p++] = (uint32_t)((pw << 5) + b);
+        }
+        pos += __shfl_sync(FULL, inc, 31);
+      }
+    }
+  }
+  return COUNT ? c : pos;
 }
 
 // Emit the row of source s (one warp): [L cols | s | U cols] into the row pool
 // at an atomically taken offset, plus the per-row counts.  swmax: the last
-// summary word that may be nonzero (global V).
-template <bool SV>
+// summary word that may be nonzero (VM_GLOBAL).
+template <int VM>
 __device__ void emit_row(const TravArgs& a, const Src& sc, const Team& tm, int nL, int diag, int rb, int re,
                          int swmax) {
   const int lane = threadIdx.x & 31;
   const int s = sc.s;
-  const int ws = s >> 5;                                  // word holding s
-  const uint32_t first_mask = (s & 31) == 31 ? 0u : (0xFFFFFFFEu << (s & 31));  // bits above s in word ws
-  const int vwords = (sc.n + 31) >> 5;
+  const uint32_t above = (s & 31) == 31 ? 0u : (0xFFFFFFFEu << (s & 31));  // bits above s in its word
   // count U(s,:)
   int nU = 1;
-  if constexpr (SV) {
-    for (int j0 = ws; j0 < vwords; j0 += 32) {
-      const int j = j0 + lane;
-      uint32_t m = j < vwords ? tm.V[j] : 0u;
-      if (j == ws) m &= first_mask;
-      int c = __popc(m);
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-      nU += c;
-    }
-  } else {
-    for (int sw0 = ws >> 5; sw0 <= swmax; sw0 += 32) {
-      const int sw = sw0 + lane;
-      uint32_t sm = sw <= swmax ? v_load<SV>(tm.VS, sw) : 0u;
-      if (sw == (ws >> 5)) sm &= 0xFFFFFFFFu << (ws & 31);
-      unsigned any = __ballot_sync(FULL, sm != 0u);
-      while (any) {
-        const int l = __ffs(any) - 1;
-        any &= any - 1;
-        const uint32_t ml = __shfl_sync(FULL, sm, l);
-        const int pw = ((sw0 + l) << 5) + lane;
-        uint32_t word = ((ml >> lane) & 1u) ? v_load<SV>(tm.V, pw) : 0u;
-        if (pw == ws) word &= first_mask;
-        int c = __popc(word);
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-        nU += c;
-      }
-    }
-  }
+  if constexpr (VM == VM_SMEM) nU += count_smem(tm.V, s >> 5, (sc.n + 31) >> 5, above, lane);
+  else nU += (int)scan_global_words<true>(tm, s >> 5, above, swmax, nullptr, 0, lane);
   unsigned long long off = 0ull;
   int ok = 0;
   if (lane == 0) {
@@ -555,68 +548,20 @@ __device__ void emit_row(const TravArgs& a, const Src& sc, const Team& tm, int n
   ok = __shfl_sync(FULL, ok, 0);
   if (!ok) return;
   for (int i = lane; i < nL; i += 32) a.pool[off + i] = (uint32_t)*l_slot(tm, i);
-  // write U(s,:) above the diagonal, in increasing order
-  long long pos = (long long)off + nL + 1;
-  if constexpr (SV) {
-    for (int j0 = ws; j0 < vwords; j0 += 32) {
-      const int j = j0 + lane;
-      uint32_t word = j < vwords ? tm.V[j] : 0u;
-      if (j == ws) word &= first_mask;
-      const int c = __popc(word);
-      int inc = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int x = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += x;
-      }
-      long long p = pos + (inc - c);
-      while (word) {
-        const int b = __ffs(word) - 1;
-        word &= word - 1;
-        a.pool[p++] = (uint32_t)((j << 5) + b);
-      }
-      pos += __shfl_sync(FULL, inc, 31);
-    }
-  } else {
-    for (int sw0 = ws >> 5; sw0 <= swmax; sw0 += 32) {
-      const int sw = sw0 + lane;
-      uint32_t sm = sw <= swmax ? v_load<SV>(tm.VS, sw) : 0u;
-      if (sw == (ws >> 5)) sm &= 0xFFFFFFFFu << (ws & 31);
-      unsigned any = __ballot_sync(FULL, sm != 0u);
-      while (any) {
-        const int l = __ffs(any) - 1;
-        any &= any - 1;
-        const uint32_t ml = __shfl_sync(FULL, sm, l);
-        const int pw = ((sw0 + l) << 5) + lane;
-        uint32_t word = ((ml >> lane) & 1u) ? v_load<SV>(tm.V, pw) : 0u;
-        if (pw == ws) word &= first_mask;
-        const int c = __popc(word);
-        int inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int x = __shfl_up_sync(FULL, inc, o);
-          if (lane >= o) inc += x;
-        }
-        long long p = pos + (inc - c);
-        while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          a.pool[p++] = (uint32_t)((pw << 5) + b);
-        }
-        pos += __shfl_sync(FULL, inc, 31);
-      }
-    }
-  }
+  // U(s,:) above the diagonal, in increasing order
+  const long long pos = (long long)off + nL + 1;
+  if constexpr (VM == VM_SMEM) write_smem(tm.V, 0, s >> 5, (sc.n + 31) >> 5, above, a.pool, pos, lane);
+  else scan_global_words<false>(tm, s >> 5, above, swmax, a.pool, pos, lane);
 }
 
-// Clear the bits the source set (threads tid, tid + nthr, ...).  Global V:
-// the summary words in [swmin, swmax] say which V words hold bits.
-template <bool SV>
-__device__ __forceinline__ void clear_v(const Team& tm, int vwords, int swmin, int swmax, int tid, int nthr) {
-  if constexpr (SV) {
-    for (int j = tid; j < vwords; j += nthr) tm.V[j] = 0u;
+// Clear the bits the source set (threads tid, tid + nthr, ...): shared words
+// all, global words through the summary words in [swmin, swmax].
+template <int VM>
+__device__ __forceinline__ void clear_v(const Team& tm, int n, int swmin, int swmax, int tid, int nthr) {
+  if constexpr (VM == VM_SMEM) {
+    for (int j = tid; j < ((n + 31) >> 5); j += nthr) tm.V[j] = 0u;
   } else {
-    if (swmin > swmax) return;  // the source set no bit (no off-diagonal neighbour)
+    if (swmin > swmax) return;  // no global bit was set
     for (int sw = swmin + tid; sw <= swmax; sw += nthr) {
       uint32_t m = tm.VS[sw];
       if (!m) continue;
@@ -628,17 +573,6 @@ __device__ __forceinline__ void clear_v(const Team& tm, int vwords, int swmin, i
       }
     }
   }
-}
-
-__device__ __forceinline__ int warp_min(int x) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) x = min(x, __shfl_xor_sync(FULL, x, o));
-  return x;
-}
-__device__ __forceinline__ int warp_max(int x) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) x = max(x, __shfl_xor_sync(FULL, x, o));
-  return x;
 }
 
 }  // namespace
@@ -674,31 +608,39 @@ __device__ __forceinline__ Src source_of(const TravArgs& a, int k) {
   return sc;
 }
 
+struct Counts {
+  unsigned long long n_exp = 0, n_edge = 0, n_lev = 0;
+  int bad = 0;
+};
+
 // One source from seeds to a cleared V.  TEAM: the whole CTA (warp 0 searches
-// classes and emits), else the calling warp.
-template <bool SV, bool TEAM>
-__device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtCtl* ctl, unsigned long long& n_exp,
-                           unsigned long long& n_edge, unsigned long long& n_lev, int& bad) {
+// classes, expands their heads and emits), else the calling warp.
+template <int VM, bool TEAM>
+__device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtCtl* ctl, Counts& cn) {
   const int lane = threadIdx.x & 31;
   const int nthr = TEAM ? CT_THREADS : 32;
   const int tid = TEAM ? (int)threadIdx.x : lane;
   const bool leader = !TEAM || threadIdx.x < 32;
   const int s = sc.s;
-  int smin = 0x7FFFFFFF, smax = -1;
+  VState st;
+  st.smin = 0x7FFFFFFF;
+  st.smax = -1;
 
   // seeds: neighbours below s are classes with maxId -1; above s, U entries
   const int rb = __ldg(sc.rowptr + s), re = __ldg(sc.rowptr + s + 1);
   int diag = 0;
   for (int e = rb + tid; e < re; e += nthr) {
     const int w = __ldg(sc.colidx + e);
-    if ((unsigned)w >= (unsigned)sc.n) { bad = 1; continue; }
+    if ((unsigned)w >= (unsigned)sc.n) { cn.bad = 1; continue; }
     if (w == s) { diag = 1; continue; }
-    v_set<SV>(tm.V, tm.VS, w, smin, smax);
+    v_set<VM>(tm, w, st);
   }
-  if constexpr (TEAM) diag = __syncthreads_or(diag);
-  else diag = __any_sync(FULL, diag);
-
-  if constexpr (!TEAM) __syncwarp();
+  if constexpr (TEAM) {
+    diag = __syncthreads_or(diag);
+  } else {
+    diag = __any_sync(FULL, diag);
+    __syncwarp();
+  }
 
   int cursor = 0, nL = 0;
   int level = 0;  // team mode: running level index (queues and counters rotate with it)
@@ -709,13 +651,13 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       // level; the counter it fills and the one it zeroes are not the one the
       // other warps may still be reading (the last level's zero length)
       if (leader) {
-        t = next_class<SV>(tm, cursor, s, lane);
+        t = next_class<VM>(tm, cursor, s, lane);
         int nq = 0;
         if (t >= 0) {
           if (lane == 0) *l_slot(tm, nL) = t;
           // the class's levels overflow into the log from its bottom
-          expand_warp<SV>(a, sc, tm, t, level, 0, 0, true, 1, nq, smin, smax, n_exp, n_edge, bad);
-          n_lev++;
+          expand<VM, false>(a, sc, tm, ctl, t, level, 0, 0, true, 1, nq, st, cn.n_exp, cn.n_edge, cn.bad);
+          cn.n_lev++;
         }
         if (lane == 0) {
           ctl->t = t;
@@ -732,17 +674,16 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       for (level++;; level++) {
         const int qlen = ctl->qcnt[level % 3];
         if (qlen == 0) break;
-        if (leader) n_lev++;
+        if (leader) cn.n_lev++;
         if (threadIdx.x == 0) ctl->qcnt[(level + 2) % 3] = 0;
         int nq_unused = 0;
         const int64_t nb = next_base(tm, cb, qlen);
-        expand_level<SV, true>(a, sc, tm, ctl, t, level, cb, nb, false, qlen, nq_unused, smin, smax, n_exp, n_edge,
-                               bad);
+        expand<VM, true>(a, sc, tm, ctl, t, level, cb, nb, false, qlen, nq_unused, st, cn.n_exp, cn.n_edge, cn.bad);
         cb = nb;
         __syncthreads();
       }
     } else {
-      t = next_class<SV>(tm, cursor, s, lane);
+      t = next_class<VM>(tm, cursor, s, lane);
       if (t < 0) break;
       cursor = t + 1;
       if (lane == 0) *l_slot(tm, nL) = t;
@@ -751,9 +692,9 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       int64_t cb = 0;  // the class's levels overflow into the log from its bottom
       for (int lv = 0; qlen > 0; lv++) {
         int nq = 0;
-        n_lev++;
+        cn.n_lev++;
         const int64_t nb = lv == 0 ? 0 : next_base(tm, cb, qlen);
-        expand_warp<SV>(a, sc, tm, t, lv, cb, nb, lv == 0, qlen, nq, smin, smax, n_exp, n_edge, bad);
+        expand<VM, false>(a, sc, tm, ctl, t, lv, cb, nb, lv == 0, qlen, nq, st, cn.n_exp, cn.n_edge, cn.bad);
         __syncwarp();
         cb = nb;
         qlen = nq;
@@ -762,10 +703,10 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
   }
 
   // the summary words this source touched
-  int swmin = smin, swmax = smax;
-  if constexpr (!SV) {
-    swmin = warp_min(smin);
-    swmax = warp_max(smax);
+  int swmin = st.smin, swmax = st.smax;
+  if constexpr (VM == VM_GLOBAL) {
+    swmin = warp_min(st.smin);
+    swmax = warp_max(st.smax);
     if constexpr (TEAM) {
       if (threadIdx.x == 0) { ctl->smin = 0x7FFFFFFF; ctl->smax = -1; }
       __syncthreads();
@@ -775,24 +716,27 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       swmax = ctl->smax;
     }
   }
-  if (leader) emit_row<SV>(a, sc, tm, nL, diag, rb, re, swmax);
+  if (leader) emit_row<VM>(a, sc, tm, nL, diag, rb, re, swmax);
   if constexpr (TEAM) __syncthreads();
   else __syncwarp();
-  clear_v<SV>(tm, (sc.n + 31) >> 5, swmin, swmax, tid, nthr);
+  clear_v<VM>(tm, sc.n, swmin, swmax, tid, nthr);
   if constexpr (TEAM) __syncthreads();
   else __syncwarp();
 }
 
 // Shared memory: control blocks (one per warp; team mode uses warp 0's), two
-// queues of qw entries per warp, then (SV) one V of vwords words per warp.
-__host__ __device__ __forceinline__ size_t ct_smem_bytes(int sv, int vwords, int qw) {
-  return (size_t)CT_WARPS * 64 + (size_t)2 * CT_WARPS * qw * 4 + (sv ? (size_t)CT_WARPS * vwords * 4 : 0);
+// queues of qw entries per warp, then (VM_SMEM) vwords bitmap words per warp.
+__host__ __device__ __forceinline__ size_t ct_smem_bytes(int vm, int vwords, int qw) {
+  return (size_t)CT_WARPS * 64 + (size_t)2 * CT_WARPS * qw * 4 +
+         (vm != VM_GLOBAL ? (size_t)CT_WARPS * vwords * 4 : 0);
 }
 
 }  // namespace
 
-// MINB: CTAs of four warps per SM the register budget is sized for.
-template <bool SV, int MINB>
+// MINB: CTAs of four warps per SM the register budget is sized for.  TEAMS:
+// the build with the CTA-team phase (only launched when ct_nbig > 0, so the
+// default build carries no team code).
+template <int VM, int MINB, bool TEAMS>
 __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -804,19 +748,18 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
   uint32_t* vsh = (uint32_t*)(q1 + CT_WARPS * qw);
   const size_t gcap = (size_t)a.g_cap;
 
-  if constexpr (SV) {
+  if constexpr (VM != VM_GLOBAL) {
     for (int j = threadIdx.x; j < CT_WARPS * vwords; j += CT_THREADS) vsh[j] = 0u;
     __syncthreads();
   }
-  unsigned long long n_exp = 0, n_edge = 0, n_lev = 0;
-  int bad = 0;
+  Counts cn;
 
   // ---- team phase: the first nbig items, one CTA per source
-  if (a.ct_nbig > 0) {
+  if (TEAMS && a.ct_nbig > 0) {
     const size_t slot = (size_t)blockIdx.x * CT_WARPS;
     Team tm;
-    tm.V = SV ? vsh : a.g_V + slot * (gcap / 32);
-    tm.VS = SV ? nullptr : a.g_VS + slot * (gcap / 1024);
+    tm.V = VM == VM_SMEM ? vsh : a.g_V + slot * (gcap / 32);
+    tm.VS = a.g_VS + slot * (gcap / 1024);
     tm.qa = q0;
     tm.qb = q1;
     tm.qcap = CT_WARPS * qw;
@@ -831,8 +774,7 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
       __syncthreads();
       const int k = ctl->src;
       if (k < 0) break;
-      const Src sc = source_of(a, k);
-      run_source<SV, true>(a, sc, tm, ctl, n_exp, n_edge, n_lev, bad);
+      run_source<VM, true>(a, source_of(a, k), tm, ctl, cn);
     }
     __syncthreads();
   }
@@ -841,8 +783,8 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
   if ((long long)blockIdx.x * CT_WARPS + warp < a.g_slots) {
     const size_t slot = (size_t)blockIdx.x * CT_WARPS + warp;
     Team tm;
-    tm.V = SV ? vsh + (size_t)warp * vwords : a.g_V + slot * (gcap / 32);
-    tm.VS = SV ? nullptr : a.g_VS + slot * (gcap / 1024);
+    tm.V = VM == VM_SMEM ? vsh + (size_t)warp * vwords : a.g_V + slot * (gcap / 32);
+    tm.VS = a.g_VS + slot * (gcap / 1024);
     tm.qa = q0 + warp * qw;
     tm.qb = q1 + warp * qw;
     tm.qcap = qw;
@@ -857,12 +799,12 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
       }
       k = __shfl_sync(FULL, k, 0);
       if (k < 0) break;
-      const Src sc = source_of(a, k);
-      run_source<SV, false>(a, sc, tm, ctl, n_exp, n_edge, n_lev, bad);
+      run_source<VM, false>(a, source_of(a, k), tm, ctl, cn);
     }
   }
 
-  if (bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
+  if (cn.bad) atomicOr(&a.ctr->err, ERR_COL_RANGE);
+  unsigned long long n_exp = cn.n_exp, n_edge = cn.n_edge;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     n_exp += __shfl_xor_sync(FULL, n_exp, o);
@@ -873,32 +815,32 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
       atomicAdd(&a.ctr->expansions, n_exp);
       atomicAdd(&a.ctr->edges, n_edge);
     }
-    atomicAdd(&a.ctr->levels, n_lev);
+    atomicAdd(&a.ctr->levels, cn.n_lev);
   }
 }
 
-size_t trav_class_smem(int sv, int vwords, int qw) { return ct_smem_bytes(sv, vwords, qw); }
+size_t trav_class_smem(int vm, int vwords, int qw) { return ct_smem_bytes(vm, vwords, qw); }
 
 namespace {
-template <bool SV, int MINB>
+template <int VM, int MINB, bool TEAMS>
 cudaError_t launch_one(const TravArgs& a, int grid, size_t smem, cudaStream_t st) {
   static int attr_set[128] = {0};  // per device: the dynamic shared-memory limit was raised
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 128 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(trav_class_kernel<SV, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(trav_class_kernel<VM, MINB, TEAMS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set[dev] = 1;
   }
-  trav_class_kernel<SV, MINB><<<grid, CT_THREADS, smem, st>>>(a);
+  trav_class_kernel<VM, MINB, TEAMS><<<grid, CT_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <bool SV, int MINB>
+template <int VM, int MINB>
 int occupancy_one(size_t smem) {
-  // answers are cached per (device, build, shared-memory size): the query is
-  // made on every plan and every server admission
+  // answers are cached per (device, shared-memory size): the query is made on
+  // every plan and every server admission
   static std::mutex mu;
   static std::map<std::tuple<int, size_t>, int> cache;
   int dev = 0;
@@ -908,9 +850,10 @@ int occupancy_one(size_t smem) {
     auto it = cache.find({dev, smem});
     if (it != cache.end()) return it->second;
   }
-  cudaFuncSetAttribute(trav_class_kernel<SV, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(trav_class_kernel<VM, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       227 * 1024);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trav_class_kernel<SV, MINB>, CT_THREADS, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trav_class_kernel<VM, MINB, false>, CT_THREADS, smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -919,23 +862,34 @@ int occupancy_one(size_t smem) {
   cache[{dev, smem}] = occ;
   return occ;
 }
+
+template <int VM>
+int occupancy_vm(int warps_per_sm, size_t smem) {
+  return warps_per_sm > 32 ? occupancy_one<VM, 10>(smem) : occupancy_one<VM, 8>(smem);
+}
+
+template <int VM>
+cudaError_t launch_vm(const TravArgs& a, int grid, int warps_per_sm, size_t smem, cudaStream_t st) {
+  if (a.ct_nbig > 0) return launch_one<VM, 8, true>(a, grid, smem, st);  // teams: the 64-register build
+  return warps_per_sm > 32 ? launch_one<VM, 10, false>(a, grid, smem, st) : launch_one<VM, 8, false>(a, grid, smem, st);
+}
 }  // namespace
 
 // CTAs of four warps per SM the class kernel reaches with this shared memory;
 // warps_per_sm above 32 selects the 48-register build.
-int trav_class_occupancy(int sv, int warps_per_sm, int vwords, int qw) {
-  const size_t smem = ct_smem_bytes(sv, vwords, qw);
+int trav_class_occupancy(int vm, int warps_per_sm, int vwords, int qw) {
+  const size_t smem = ct_smem_bytes(vm, vwords, qw);
   if (smem > 227 * 1024) return 0;
-  if (warps_per_sm > 32) return sv ? occupancy_one<true, 10>(smem) : occupancy_one<false, 10>(smem);
-  return sv ? occupancy_one<true, 8>(smem) : occupancy_one<false, 8>(smem);
+  if (vm == VM_SMEM) return occupancy_vm<VM_SMEM>(warps_per_sm, smem);
+  return occupancy_vm<VM_GLOBAL>(warps_per_sm, smem);
 }
 
-cudaError_t launch_trav_class(const TravArgs& a, int grid, int sv, int warps_per_sm, cudaStream_t st) {
+cudaError_t launch_trav_class(const TravArgs& a, int grid, int vm, int warps_per_sm, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  const size_t smem = ct_smem_bytes(sv, a.ct_vwords, a.ct_qw);
+  const size_t smem = ct_smem_bytes(vm, a.ct_vwords, a.ct_qw);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  if (warps_per_sm > 32) return sv ? launch_one<true, 10>(a, grid, smem, st) : launch_one<false, 10>(a, grid, smem, st);
-  return sv ? launch_one<true, 8>(a, grid, smem, st) : launch_one<false, 8>(a, grid, smem, st);
+  if (vm == VM_SMEM) return launch_vm<VM_SMEM>(a, grid, warps_per_sm, smem, st);
+  return launch_vm<VM_GLOBAL>(a, grid, warps_per_sm, smem, st);
 }
 
 }  // namespace gsofa
