@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--requests", type=int, default=20000, help="served: stream length")
     ap.add_argument("--rate-frac", type=float, default=0.7, help="served: arrival rate / saturated req/s")
+    ap.add_argument("--streams", type=int, default=2, help="served: server stream slots")
+    ap.add_argument("--max-batch", type=int, default=512, help="served: requests per batch at most")
     ap.add_argument("--opt", action="append", default=[], help="library option NAME=VALUE (repeatable)")
     return ap.parse_args()
 
@@ -575,7 +577,7 @@ def run_served_bench(args, rank, world, local):
     nreq = args.requests
     burst = min(2000, nreq)
     which_b, _ = synth.served_choices(burst, len(small), len(big), seed=5)
-    srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30)
+    srv = gs.Server(streams=args.streams, max_batch=args.max_batch, mem_cap_bytes=150 << 30)
     t0 = time.perf_counter()
     tk = [srv.submit(*dpool[int(k)]) for k in which_b]
     for t_ in tk:
@@ -589,7 +591,7 @@ def run_served_bench(args, rank, world, local):
     # on the device after the stream (the comparison is outside the latency)
     ref = [gs.symbolic_device(*d) for d in dpool]
     torch.cuda.synchronize(dev)
-    srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30, opts=gs.options())
+    srv = gs.Server(streams=args.streams, max_batch=args.max_batch, mem_cap_bytes=150 << 30, opts=gs.options())
     sampler = ClockSampler(local)
     sampler.start()
     tickets = []
@@ -600,8 +602,10 @@ def run_served_bench(args, rank, world, local):
             pass
         tickets.append(srv.submit(*dpool[int(which[i])]))
     mismatches = 0
+    lat_small, lat_large = [], []
     for i, t in enumerate(tickets):
-        r, _ = srv.wait(t, keep_result=True)
+        r, lat = srv.wait(t, keep_result=True)
+        (lat_large if int(which[i]) >= len(small) else lat_small).append(lat)
         g = ref[int(which[i])]
         for f in ("L_rowptr", "L_colidx", "U_rowptr", "U_colidx", "fill_count", "super_start"):
             if not torch.equal(getattr(r, f), getattr(g, f)):
@@ -619,7 +623,7 @@ def run_served_bench(args, rank, world, local):
         ne = min(2000, nreq)
         hpool = [(torch.from_numpy(A.rowptr).pin_memory().numpy(), torch.from_numpy(A.colidx).pin_memory().numpy())
                  for A in pool]
-        srv = gs.Server(streams=2, max_batch=512, mem_cap_bytes=150 << 30, opts=gs.options())
+        srv = gs.Server(streams=args.streams, max_batch=args.max_batch, mem_cap_bytes=150 << 30, opts=gs.options())
         h2d = d2h = nnz_e = 0
         tickets = []
         start = time.perf_counter()
@@ -658,11 +662,17 @@ def run_served_bench(args, rank, world, local):
                    "rate": f"{args.rate_frac} x saturated served throughput ({sat_rps:.1f} req/s; batched small "
                            f"{1000 * t_small:.3f} ms/request, large alone {1000 * t_big:.1f} ms)",
                    "batched_small_req_per_s": batched_rps, "big_fraction": 0.02,
-                   "mem_cap_bytes": 150 << 30, "streams": 2, "max_batch": 512},
+                   "mem_cap_bytes": 150 << 30, "streams": args.streams, "max_batch": args.max_batch},
         "requests_per_s": completed / span, "rows_per_s": total_rows / span, "e2e": e2e,
         "gpu_launches": int(launches_all), "latency_scope": "rank 0" if world > 1 else "all requests",
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "batches": st["batches"],
-        "peak_projected_mem_bytes": st["peak_mem_in_use"], "completed": st["completed"], "failed": st["failed"],
+        "peak_projected_mem_bytes": st["peak_mem_in_use"], "peak_device_bytes": st["peak_device_bytes"],
+        "completed": st["completed"], "failed": st["failed"],
+        "latency_by_kind_ms": {
+            "small": {"count": len(lat_small), "p50": float(np.percentile(lat_small, 50)) if lat_small else None,
+                      "p99": float(np.percentile(lat_small, 99)) if lat_small else None},
+            "large_nd512": {"count": len(lat_large), "p50": float(np.percentile(lat_large, 50)) if lat_large else None,
+                            "p99": float(np.percentile(lat_large, 99)) if lat_large else None}},
         "checked_against_alone": nreq, "mismatches": mismatches, "wall_s": wall, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

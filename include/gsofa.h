@@ -208,16 +208,23 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
 /*
  * Serving (an extension built on the Section 4/5 method): a request loop
  * that factors incoming sparsity patterns with continuous batching.
- * Requests are admitted in arrival order while their projected device memory
- * (CSR copy, per-row workspace, row pool and outputs, label slots of large
- * orders) fits under mem_cap_bytes; each of `streams` slots runs the admitted
- * requests waiting at that moment (up to max_batch) as one multi-matrix batch.
- * A slot launches as soon as it is free, so the next batch queues on the GPU
- * behind the running one and their phases overlap (opts.max_ctas can split
- * the GPU between slots instead).  A request whose label slots alone would
- * exceed the cap runs alone with as many slots as the cap leaves room for
- * (space-budget mode: fewer sources in flight, same result); one that does
- * not fit even with one slot is refused with GSOFA_E_NOMEM.
+ * Requests are admitted in arrival order while the server's device memory fits
+ * under mem_cap_bytes: each admitted request is charged its projected bytes
+ * (CSR copy, per-row workspace, row pool and outputs, class-kernel slots of
+ * large orders), each running batch the class-kernel slots it uses (fewer
+ * slots when the cap leaves less room), and each completed result its size
+ * until the caller collects it (a batch's results share one block, released
+ * with the last of them; uncollected results therefore hold admission back).
+ * Admitted requests wait in two queues, batchable orders (visited bitmaps on
+ * chip) and large ones; a free slot of `streams` takes whichever holds the
+ * oldest request: all waiting batchable requests (up to max_batch) as one
+ * multi-matrix batch, or one large request alone, so a large request never
+ * holds up the small ones.  Slots launch as soon as they are free, so their
+ * work overlaps on the GPU (opts.max_ctas can split the GPU between slots
+ * instead).  A request whose slots alone would exceed the cap runs alone with
+ * as many slots as the cap leaves room for (space-budget mode: fewer sources in
+ * flight, same result); one that does not fit even with one slot is refused
+ * with GSOFA_E_NOMEM.
  */
 typedef struct gsofa_server gsofa_server;
 
@@ -236,10 +243,14 @@ typedef struct gsofa_server_stats {
     int32_t kernel_launches;     /* library kernels launched for completed batches (saturates) */
     int64_t total_nnz;           /* nnz(L+U) of completed requests */
     int64_t total_rows;          /* rows of completed requests */
-    int64_t mem_in_use, peak_mem_in_use;   /* projected bytes of admitted requests */
+    int64_t mem_in_use, peak_mem_in_use;   /* projected bytes of admitted requests and running batches */
     float p50_ms, p99_ms, max_ms;          /* latency, submission to completed result */
     float pad2;
     double span_s;               /* first submission to last completion */
+    int64_t peak_device_bytes;   /* device memory the server's work held at its peak, beyond what the
+                                    library held when the server started: stream-ordered pool high-water
+                                    mark (uncollected results included), class-kernel slots it made the
+                                    library keep, and copies of host inputs */
 } gsofa_server_stats;
 
 int gsofa_server_default_config(gsofa_server_config *cfg);

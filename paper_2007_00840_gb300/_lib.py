@@ -110,6 +110,7 @@ class gsofa_server_stats(ctypes.Structure):
         ("max_ms", ctypes.c_float),
         ("pad2", ctypes.c_float),
         ("span_s", ctypes.c_double),
+        ("peak_device_bytes", ctypes.c_int64),
     ]
 
 

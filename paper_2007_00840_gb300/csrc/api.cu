@@ -190,8 +190,8 @@ void pfree(T*& p, cudaStream_t st) {
 
 // First row-pool size for `rows` rows whose full rows hold at most `full`
 // entries: per row, the larger of `floor_per_row` and 1.25 x the largest ratio
-// seen on this device, so a stream of similar patterns stops overflowing (an
-// overflow reruns the traversal).
+// seen on this device, plus 64K entries, so a stream of similar patterns stops
+// overflowing (an overflow reruns the traversal).
 long long pool_estimate(Ctx* c, long long rows, long long floor_per_row, long long full) {
   double per_row;
   {
@@ -199,7 +199,7 @@ long long pool_estimate(Ctx* c, long long rows, long long floor_per_row, long lo
     per_row = 1.25 * c->rows_ratio;
   }
   if (per_row < (double)floor_per_row) per_row = (double)floor_per_row;
-  long long cap = (long long)(per_row * (double)rows) + (1 << 20);
+  long long cap = (long long)(per_row * (double)rows) + (1 << 16);
   if (full > 0 && cap > full) cap = full;
   if (cap < 1024) cap = 1024;
   return cap;
@@ -1418,7 +1418,9 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
     {
       std::lock_guard<std::mutex> lk(bc.mu);
       load_tune_file(bc);
-      const LaunchShape sh = default_shape(c, bc, p, o, limit, &rc);
+      LaunchShape sh = default_shape(c, bc, p, o, limit, &rc);
+      // a caller's cap on sources in flight (a server's memory share) bounds the slots
+      if (sh.kernel == 1 && o.max_concurrent > 0 && sh.slots > o.max_concurrent) sh.slots = o.max_concurrent;
       if (rc == GSOFA_OK) rc = set_shape(c, p, sh);
     }
     if (rc == GSOFA_OK) rc = batch_phase1(c, p, o, st, false, launches);
@@ -1531,6 +1533,37 @@ int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, c
 }
 
 int64_t global_slot_bytes(int32_t n) { return slot_bytes(((int64_t)n + 1023) / 1024 * 1024); }
+
+int32_t batch_class_slots(int32_t n_max) {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  return c ? class_slots(c, n_max, 40) : 0;
+}
+
+int64_t library_pool_bytes(int high, int reset_high) {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return 0;
+  uint64_t v = 0;
+  if (cudaMemPoolGetAttribute(c->mpool, high ? cudaMemPoolAttrUsedMemHigh : cudaMemPoolAttrUsedMemCurrent, &v) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  if (reset_high) {
+    uint64_t z = 0;
+    cudaMemPoolSetAttribute(c->mpool, cudaMemPoolAttrUsedMemHigh, &z);
+  }
+  return (int64_t)v;
+}
+
+int64_t library_slot_bytes() {
+  int err = GSOFA_OK;
+  Ctx* c = get_ctx(&err);
+  if (!c) return 0;
+  std::lock_guard<std::mutex> lk(c->gmu);
+  return c->g_V ? (int64_t)c->g_slots * slot_bytes(c->g_cap) : 0;
+}
 
 int64_t global_tier_bytes(int32_t n, const gsofa_options* opts) {
   int err = GSOFA_OK;

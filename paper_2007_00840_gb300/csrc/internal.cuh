@@ -166,6 +166,13 @@ int64_t global_tier_bytes(int32_t n, const gsofa_options* opts);
 int64_t global_slot_bytes(int32_t n);
 void detach_result_stream(gsofa_result* r);
 int32_t smem_tier_max_order();
+// Class-kernel slots an untuned batch of largest order n_max would use.
+int32_t batch_class_slots(int32_t n_max);
+// Bytes of the library's stream-ordered pool in use now (high 0) or at its
+// high-water mark (high 1; reset_high 1 restarts the mark).
+int64_t library_pool_bytes(int high, int reset_high);
+// Bytes held by the single-matrix class-kernel slots (kept between calls).
+int64_t library_slot_bytes();
 int wait_stream(cudaStream_t st);  // bounded wait; GSOFA_OK / GSOFA_E_TIMEOUT / GSOFA_E_CUDA
 int choose_smem_config(int sms, size_t limit, int32_t n, int32_t S, int label16, int threads_req, int* block,
                        int* occ, int32_t* cap);

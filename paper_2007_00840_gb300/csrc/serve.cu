@@ -1,15 +1,19 @@
 // Serving: continuous batching of incoming sparsity patterns.
 //
 // Requests are admitted in arrival order while their projected device memory
-// (CSR copy, per-row workspace, row pool and outputs, global-tier label slots
-// for large orders) fits under the configured cap.  Each of `streams` stream
-// slots has a dispatcher thread that takes the admitted requests waiting at
-// that moment (up to max_batch) and runs them as one batch (the multi-matrix
-// traversal of gsofa_batch, with pooled workspace).  While one slot's batch is
-// on the GPU the other slot gathers the requests that arrived meanwhile and
-// launches them behind it (its CTAs start as the running batch's CTAs retire,
-// and its size read-back and output assembly overlap the other batch's
-// traversal), so requests start as soon as a slot and memory free up.  Latency
+// (CSR copy, per-row workspace, row pool and outputs, class-kernel slots for
+// large orders) fits under the configured cap.  Admitted requests wait in two
+// queues: batchable ones (orders whose visited bitmaps fit on chip) and large
+// ones.  Each of `streams` stream slots has a dispatcher thread; a free slot
+// takes whichever queue holds the oldest request: every batchable request
+// waiting at that moment (up to max_batch) as one batch (the multi-matrix
+// traversal of gsofa_batch, with pooled workspace), or one large request alone
+// on a high-priority stream and half of the traversal CTAs.  So a large request
+// occupies one slot and part of the GPU while the others keep serving batches,
+// instead of holding up the small requests batched with it.  While one slot's
+// work is on the GPU another gathers the requests that arrived meanwhile and
+// launches them beside it.  A batch's class-kernel slots are charged against
+// the cap while it runs (fewer slots when the cap leaves less room).  Latency
 // is measured from submission to completion of the result.
 #include <algorithm>
 #include <chrono>
@@ -29,6 +33,14 @@ using Clock = std::chrono::steady_clock;
 namespace gsofa {
 namespace {
 
+// Device bytes of the results of one batch (or one large request), charged
+// against the cap from completion until the last of them is collected: batch
+// results share one block that is freed with the last member.
+struct Charge {
+  int64_t bytes = 0;
+  int refs = 0;
+};
+
 struct Request {
   uint64_t ticket = 0;
   int32_t n = 0;
@@ -40,6 +52,8 @@ struct Request {
   int32_t* own = nullptr;           // server copy of a host CSR (rowptr then colidx)
   int64_t projected = 0;
   int64_t budget = 0;               // space-budget mode: mem_budget_bytes of this request (0: server default)
+  bool big = false;                 // runs alone (order above the on-chip limit)
+  Charge* held = nullptr;           // result bytes charged until collected
   Clock::time_point t_submit, t_done;
   bool done = false;
   int status = GSOFA_OK;
@@ -59,17 +73,20 @@ struct gsofa_server {
   cudaMemPool_t mpool = nullptr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<Request*> pending, ready;
+  std::deque<Request*> pending, ready_small, ready_big;
   std::unordered_map<uint64_t, Request*> live;
   int64_t in_use = 0;
   int32_t inflight = 0;
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;       // per slot: batches
+  std::vector<cudaStream_t> streams_hi;    // per slot: large requests, at the highest stream priority
   // statistics
   int64_t completed = 0, failed = 0, batches = 0, total_nnz = 0, total_rows = 0, launches = 0;
   int64_t peak_in_use = 0;
+  // device memory actually held: library pool at start, class slots at start, peak seen
+  int64_t pool_base = 0, slots_base = 0, peak_device = 0;
   std::vector<float> lat_ms;
   bool have_first = false;
   Clock::time_point t_first, t_last;
@@ -97,29 +114,68 @@ void admit(gsofa_server* S) {
     S->in_use += r->projected;
     if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
     S->inflight++;
-    S->ready.push_back(r);
+    (r->big ? S->ready_big : S->ready_small).push_back(r);
   }
+}
+
+// Device memory the server's work holds beyond what was held when it started:
+// the library pool's high-water mark, class slots it made the library keep,
+// and its own pool (host inputs).  Caller holds mu.
+void sample_device(gsofa_server* S) {
+  int64_t lib = library_pool_bytes(1, 0) - S->pool_base;
+  if (lib < 0) lib = 0;
+  int64_t slots = library_slot_bytes() - S->slots_base;
+  if (slots < 0) slots = 0;
+  uint64_t own = 0;
+  if (cudaMemPoolGetAttribute(S->mpool, cudaMemPoolAttrUsedMemHigh, &own) != cudaSuccess) {
+    cudaGetLastError();
+    own = 0;
+  }
+  const int64_t d = lib + slots + (int64_t)own;
+  if (d > S->peak_device) S->peak_device = d;
 }
 
 void worker_loop(gsofa_server* S, int slot) {
   cudaSetDevice(S->device);
-  cudaStream_t st = S->streams[slot];
   std::vector<Request*> take;
   std::vector<int32_t> ns;
   std::vector<const int32_t*> rps, cis;
   std::vector<gsofa_result> outs;
   for (;;) {
     take.clear();
+    int64_t reserved = 0;   // class-slot bytes of a batch, charged while it runs
+    int32_t batch_slots = 0;
+    bool small = false;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !S->ready.empty(); });
-      if (S->ready.empty() && S->stop) return;
-      while (!S->ready.empty() && (int)take.size() < S->cfg.max_batch) {
-        take.push_back(S->ready.front());
-        S->ready.pop_front();
+      S->cv_work.wait(lk, [&] { return S->stop || !S->ready_small.empty() || !S->ready_big.empty(); });
+      if (S->ready_small.empty() && S->ready_big.empty() && S->stop) return;
+      // the queue with the oldest request goes first
+      small = !S->ready_small.empty() &&
+              (S->ready_big.empty() || S->ready_small.front()->t_submit <= S->ready_big.front()->t_submit);
+      if (small) {
+        int32_t nmax = 0;
+        while (!S->ready_small.empty() && (int)take.size() < S->cfg.max_batch) {
+          take.push_back(S->ready_small.front());
+          nmax = std::max(nmax, S->ready_small.front()->n);
+          S->ready_small.pop_front();
+        }
+        // the batch's class-kernel slots: as many as the cap leaves room for
+        const int64_t per = global_slot_bytes(nmax);
+        batch_slots = batch_class_slots(nmax);
+        const int64_t room = S->cfg.mem_cap_bytes - S->in_use;
+        if (per > 0 && (int64_t)batch_slots * per > room) batch_slots = (int32_t)std::max<int64_t>(4, room / per);
+        reserved = (int64_t)batch_slots * per;
+        S->in_use += reserved;
+        if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
+      } else {
+        take.push_back(S->ready_big.front());
+        S->ready_big.pop_front();
       }
     }
-    // host inputs: copy into pooled device memory on this slot's stream
+    // batches on the slot's stream, a large request on its high-priority one
+    cudaStream_t st = small ? S->streams[slot] : S->streams_hi[slot];
+    // host inputs: copy into pooled device memory on that stream
     const int k = (int)take.size();
     std::vector<int> rcs(k, GSOFA_OK);
     for (int i = 0; i < k; i++) {
@@ -138,19 +194,6 @@ void worker_loop(gsofa_server* S, int slot) {
       r->ci = r->own + r->n + 1;
     }
     outs.assign(k, gsofa_result());
-    // requests admitted in space-budget mode run alone with their own budget;
-    // the others run as one batch
-    ns.clear();
-    rps.clear();
-    cis.clear();
-    std::vector<int> in_batch;
-    for (int i = 0; i < k; i++) {
-      if (take[i]->budget > 0 || rcs[i] != GSOFA_OK) continue;
-      in_batch.push_back(i);
-      ns.push_back(take[i]->n);
-      rps.push_back(take[i]->rp);
-      cis.push_back(take[i]->ci);
-    }
     int64_t launches = 0;
     auto run_alone = [&](int i, const gsofa_options& o) {
       const int32_t n1 = take[i]->n;
@@ -159,26 +202,44 @@ void worker_loop(gsofa_server* S, int slot) {
       rcs[i] = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i]);
       if (rcs[i] == GSOFA_OK) launches += outs[i].stats.kernel_launches;
     };
-    if (!in_batch.empty()) {
-      std::vector<gsofa_result> bo(in_batch.size());
-      const int brc =
-          batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &S->cfg.opts, st, bo.data());
-      if (brc == GSOFA_OK) {
-        launches += bo[0].stats.kernel_launches;  // the batch's total
-        for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
-      } else if (brc == GSOFA_E_INVAL && in_batch.size() > 1) {
-        // a malformed pattern rejects the whole batch: run the members one by
-        // one so that only the offending request fails, as it would alone
-        for (int i : in_batch) run_alone(i, S->cfg.opts);
-      } else {
-        for (int i : in_batch) rcs[i] = brc;
+    if (small) {
+      // one batch of the small requests
+      ns.clear();
+      rps.clear();
+      cis.clear();
+      std::vector<int> in_batch;
+      for (int i = 0; i < k; i++) {
+        if (rcs[i] != GSOFA_OK) continue;
+        in_batch.push_back(i);
+        ns.push_back(take[i]->n);
+        rps.push_back(take[i]->rp);
+        cis.push_back(take[i]->ci);
       }
-    }
-    for (int i = 0; i < k; i++) {
-      if (take[i]->budget == 0 || rcs[i] != GSOFA_OK) continue;
+      gsofa_options bo_opts = S->cfg.opts;
+      if (batch_slots > 0) bo_opts.max_concurrent = batch_slots;
+      if (!in_batch.empty()) {
+        std::vector<gsofa_result> bo(in_batch.size());
+        const int brc =
+            batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &bo_opts, st, bo.data());
+        if (brc == GSOFA_OK) {
+          launches += bo[0].stats.kernel_launches;  // the batch's total
+          for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
+        } else if (brc == GSOFA_E_INVAL && in_batch.size() > 1) {
+          // a malformed pattern rejects the whole batch: run the members one by
+          // one so that only the offending request fails, as it would alone
+          for (int i : in_batch) run_alone(i, bo_opts);
+        } else {
+          for (int i : in_batch) rcs[i] = brc;
+        }
+      }
+    } else if (rcs[0] == GSOFA_OK) {
+      // one large request alone (space-budget mode: with its own memory budget),
+      // on half of the traversal CTAs so that batches keep running beside it:
+      // its time is set by the serial class chains of its largest sources
       gsofa_options o = S->cfg.opts;
-      o.mem_budget_bytes = take[i]->budget;
-      run_alone(i, o);
+      if (take[0]->budget > 0) o.mem_budget_bytes = take[0]->budget;
+      if (o.max_ctas == 0) o.max_ctas = S->sms * 4;
+      run_alone(0, o);
     }
     const int wrc = wait_stream(st);  // results complete
     for (int i = 0; i < k; i++) {
@@ -193,13 +254,28 @@ void worker_loop(gsofa_server* S, int slot) {
         r->own = nullptr;
       }
     std::lock_guard<std::mutex> lk(S->mu);
+    sample_device(S);
     S->batches++;
     S->launches += launches;
+    S->in_use -= reserved;
+    Charge* ch = nullptr;
+    for (int i = 0; i < k; i++) {
+      if (rcs[i] != GSOFA_OK) continue;
+      if (!ch) ch = new Charge();
+      const gsofa_result& o = outs[i];
+      ch->bytes += 16 * ((int64_t)o.n + 1) + 4 * (o.nnz_L + o.nnz_U) + 4 * (int64_t)o.n + 4 * ((int64_t)o.n_super + 1);
+      ch->refs++;
+    }
+    if (ch) {
+      S->in_use += ch->bytes;
+      if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
+    }
     for (int i = 0; i < k; i++) {
       Request* r = take[i];
       r->t_done = now;
       r->status = rcs[i];
       if (rcs[i] == GSOFA_OK) {
+        r->held = ch;
         r->res = outs[i];
         S->completed++;
         S->total_nnz += outs[i].nnz_L + outs[i].nnz_U;
@@ -272,16 +348,28 @@ int gsofa_server_create(const gsofa_server_config* cfg, gsofa_server** out) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(S->mpool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    prio_lo = prio_hi = 0;
+  }
   for (int i = 0; i < S->cfg.streams; i++) {
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t st = nullptr, sh = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sh, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+      cudaGetLastError();
+      if (st) cudaStreamDestroy(st);
       for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+      for (cudaStream_t x : S->streams_hi) cudaStreamDestroy(x);
       cudaMemPoolDestroy(S->mpool);
       delete S;
       return GSOFA_E_CUDA;
     }
     S->streams.push_back(st);
+    S->streams_hi.push_back(sh);
   }
+  S->pool_base = library_pool_bytes(0, 1);  // in use now; the high-water mark restarts here
+  S->slots_base = library_slot_bytes();
   for (int i = 0; i < S->cfg.streams; i++) S->workers.emplace_back(worker_loop, S, i);
   *out = S;
   return GSOFA_OK;
@@ -320,6 +408,7 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
     }
   }
   if (r->projected > S->cfg.mem_cap_bytes) { delete r; return GSOFA_E_NOMEM; }
+  r->big = n > S->smem_max_n || r->budget > 0;
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) { delete r; return GSOFA_E_INVAL; }
   if ((int64_t)S->pending.size() >= S->cfg.queue_capacity) { delete r; return GSOFA_E_BUSY; }
@@ -334,12 +423,24 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
   return GSOFA_OK;
 }
 
+// Caller holds mu.
+static void release_charge(gsofa_server* S, Request* r) {
+  Charge* ch = r->held;
+  r->held = nullptr;
+  if (!ch || --ch->refs > 0) return;
+  S->in_use -= ch->bytes;
+  delete ch;
+  admit(S);
+  S->cv_work.notify_all();
+}
+
 static int take_result(gsofa_server* S, std::unordered_map<uint64_t, Request*>::iterator it, gsofa_result* out,
                        double* latency_ms) {
   Request* r = it->second;
   const int st = r->status;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   if (out) *out = r->res; else gsofa_free(&r->res);
+  release_charge(S, r);
   S->live.erase(it);
   delete r;
   return st;
@@ -379,6 +480,8 @@ int gsofa_server_get_stats(gsofa_server* S, gsofa_server_stats* st) {
   st->total_rows = S->total_rows;
   st->mem_in_use = S->in_use;
   st->peak_mem_in_use = S->peak_in_use;
+  sample_device(S);
+  st->peak_device_bytes = S->peak_device;
   st->p50_ms = percentile(S->lat_ms, 0.50);
   st->p99_ms = percentile(S->lat_ms, 0.99);
   st->max_ms = percentile(S->lat_ms, 1.0);
@@ -402,9 +505,14 @@ void gsofa_server_destroy(gsofa_server* S) {
   for (std::thread& t : S->workers) t.join();
   for (auto& kv : S->live) {
     gsofa_free(&kv.second->res);
+    release_charge(S, kv.second);
     delete kv.second;
   }
   for (cudaStream_t st : S->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaStream_t st : S->streams_hi) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }

@@ -86,7 +86,10 @@ def test_admission_cap_busy_and_oversize():
     with pytest.raises(gs.GsofaError) as ei:
         srv.submit(*to_device(big))
     assert ei.value.code == -2
-    assert srv.stats()["peak_mem_in_use"] <= 64 << 20
+    st = srv.stats()
+    assert st["peak_mem_in_use"] <= 64 << 20
+    # device memory the served work actually held (pool high-water mark, slots, input copies)
+    assert 0 < st["peak_device_bytes"] <= 64 << 20, st["peak_device_bytes"]
     srv.close()
 
 
@@ -119,6 +122,7 @@ def test_space_budget_admission():
     st = srv.stats()
     assert st["completed"] == 7 and st["failed"] == 0
     assert st["peak_mem_in_use"] <= cap
+    assert 0 < st["peak_device_bytes"] <= cap, st["peak_device_bytes"]
     srv.close()
 
 
