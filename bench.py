@@ -448,7 +448,7 @@ def run_batch_bench(args, rank, world, local):
         if len(f) >= 7:
             tuned = {"threads_per_source": int(f[1]), "ctas_per_sm": int(f[2]), "list_capacity": int(f[3]),
                      "work_chunk": int(f[4]), "kernel": ["cta_per_source_bfs", "warp_per_source_class"][int(f[5])],
-                     "class_slots": int(f[6])}
+                     "class_slots": int(f[6]), "fill_first": int(f[7]) if len(f) >= 8 else 0}
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()

@@ -67,8 +67,9 @@ typedef struct gsofa_options {
     int32_t validate;            /* 0 or 1: check the CSR on the device first (default 1); 2: skip */
     int32_t autotune;            /* 1 = time candidates once and keep the fastest: gsofa_batch per batch shape
                                     (kernel, block size, CTAs or warps per SM, frontier list capacity,
-                                    work items per fetch); single matrices per (n, nnz) (frontier
-                                    order).  0 = heuristic choices */
+                                    work items per fetch, the fill-first check); single matrices per
+                                    (n, nnz) (frontier order, and the fill-first check for breadth-first).
+                                    0 = heuristic choices */
     int32_t work_chunk;          /* work items a CTA takes per fetch (default 1) */
     int32_t list_capacity;       /* frontier list entries kept in shared memory (default 2,048, fewer if the
                                     occupancy needs it; the rest spills to global memory) */

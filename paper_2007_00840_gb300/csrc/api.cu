@@ -517,7 +517,7 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
 
 // ---------------------------------------------------------------- one matrix
 int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx, const gsofa_options& o,
-               cudaStream_t st, gsofa_result* out) {
+               cudaStream_t st, gsofa_result* out, int64_t pool_entries = 0) {
   zero_result(out);
   Priv* pv = new Priv();
   pv->stream = st;
@@ -581,6 +581,8 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     auto it = c->pool_hint.find(n);
     if (it != c->pool_hint.end()) pool_cap = it->second;
   }
+  // first size: the caller's estimate (a server's charge), else the learned ratio
+  if (pool_cap == 0 && pool_entries > 0) pool_cap = pool_entries + (1 << 16);
   if (pool_cap == 0) pool_cap = pool_estimate(c, n, 256, (long long)n * (long long)(n + 1));
   CK(palloc(c, &pool, (size_t)pool_cap, st));
   if (plan.S > 0) {
@@ -772,6 +774,7 @@ struct LaunchShape {
   int work_chunk = 1;
   int kernel = 0;   // 0: shared-memory breadth-first tier; 1: class-ordered warp tier
   int slots = 0;    // kernel 1: warps (sources in flight)
+  int fill_first = 0;  // kernel 0: the fill-first check of Section 4 ("line 9.5"; same rows)
 };
 
 // Workspace and captured graph of one batch signature.
@@ -888,11 +891,11 @@ void load_tune_file(BatchCache& bc) {
   FILE* fp = std::fopen(f, "r");
   if (!fp) return;
   unsigned long long key;
-  int block, occ, cap, chunk, kernel, slots;
-  while (std::fscanf(fp, "%llx %d %d %d %d %d %d", &key, &block, &occ, &cap, &chunk, &kernel, &slots) == 7) {
+  int block, occ, cap, chunk, kernel, slots, ff;
+  while (std::fscanf(fp, "%llx %d %d %d %d %d %d %d", &key, &block, &occ, &cap, &chunk, &kernel, &slots, &ff) == 8) {
     LaunchShape sh;
     sh.block = block; sh.occ = occ; sh.list_cap = cap; sh.work_chunk = chunk;
-    sh.kernel = kernel; sh.slots = slots;
+    sh.kernel = kernel; sh.slots = slots; sh.fill_first = ff;
     bc.tuned[key] = sh;
   }
   std::fclose(fp);
@@ -904,9 +907,9 @@ void save_tune_entry(uint64_t key, const LaunchShape& sh) {
   FILE* fp = std::fopen(f, "a");
   if (!fp) return;
   // key, threads per source, CTAs per SM, list capacity, work chunk, kernel (0 CTA per
-  // source, 1 class-ordered warp per source), class-kernel slots
-  std::fprintf(fp, "%llx %d %d %d %d %d %d\n", (unsigned long long)key, sh.block, sh.occ, sh.list_cap,
-               sh.work_chunk, sh.kernel, sh.slots);
+  // source, 1 class-ordered warp per source), class-kernel slots, fill-first check
+  std::fprintf(fp, "%llx %d %d %d %d %d %d %d\n", (unsigned long long)key, sh.block, sh.occ, sh.list_cap,
+               sh.work_chunk, sh.kernel, sh.slots, sh.fill_first);
   std::fclose(fp);
 }
 
@@ -936,6 +939,10 @@ std::vector<LaunchShape> candidate_shapes(Ctx* c, int32_t n_max, int label16, si
         LaunchShape sh;
         sh.block = block; sh.occ = occ; sh.list_cap = caps[ci]; sh.work_chunk = chunk;
         out.push_back(sh);
+        if (chunk == 1) {  // the same shape with the fill-first check
+          sh.fill_first = 1;
+          out.push_back(sh);
+        }
       }
     }
   }
@@ -971,7 +978,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.row_nU = p.row_nU;
   a.fill_count = p.fill;
   a.ctr = p.ctr();
-  a.fill_first = o.fill_first;
+  a.fill_first = (o.fill_first || p.shape.fill_first) ? 1 : 0;
   a.collect_stats = o.collect_stats;
   a.mats = p.d_mats;
   a.item_start = p.d_item_start;
@@ -1078,7 +1085,7 @@ void* thread_pinned(size_t bytes, int slot) {
 
 int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
                const int32_t* const* ci, const gsofa_options& o, uint64_t sig, BatchPlan** out,
-               bool transient, cudaStream_t st) {
+               bool transient, cudaStream_t st, int64_t pool_entries = 0) {
   BatchPlan* p = new BatchPlan();
   p->transient = transient;
   p->stream = st;
@@ -1135,6 +1142,7 @@ int build_plan(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, co
     auto it = c->pool_hint.find(-(int32_t)(sig & 0x7FFFFFFF) - 1);
     p->pool_cap = it != c->pool_hint.end() ? it->second : 0;
   }
+  if (p->pool_cap == 0 && pool_entries > 0) p->pool_cap = pool_entries + (1 << 16);
   if (p->pool_cap == 0) p->pool_cap = pool_estimate(c, p->N, 64, 0);
   if (transient) {
     const size_t b_mats = sizeof(MatDesc) * (size_t)(p->B > 0 ? p->B : 1);
@@ -1407,13 +1415,16 @@ LaunchShape default_shape(Ctx* c, BatchCache& bc, const BatchPlan* p, const gsof
 // one-off composition (served batches): pooled workspace, no graph, no cache.
 int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t* n, const int32_t* const* rp,
                       const int32_t* const* ci, const gsofa_options& o, cudaStream_t st, gsofa_result* outs,
-                      int* launches, bool transient) {
+                      int* launches, bool transient, const int64_t* pool_entries) {
   BatchCache& bc = g_batch[c->device];
   const int stat = trav_smem_static_bytes();
   const size_t limit = (size_t)c->smem_optin - (size_t)stat - 64;
   if (transient) {
     BatchPlan* p = nullptr;
-    int rc = build_plan(c, members, n, rp, ci, o, 0, &p, true, st);
+    int64_t pe = 0;
+    if (pool_entries)
+      for (int32_t k : members) pe += pool_entries[k];
+    int rc = build_plan(c, members, n, rp, ci, o, 0, &p, true, st, pe);
     if (rc) return rc;
     {
       std::lock_guard<std::mutex> lk(bc.mu);
@@ -1484,7 +1495,8 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
 }
 
 int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
-              const gsofa_options& o, cudaStream_t st, gsofa_result* outs, bool transient) {
+              const gsofa_options& o, cudaStream_t st, gsofa_result* outs, bool transient,
+              const int64_t* pool_entries = nullptr) {
   for (int32_t k = 0; k < count; k++) zero_result(&outs[k]);
   // members: matrices whose every source fits the shared-memory tier together
   const int stat = trav_smem_static_bytes();
@@ -1504,10 +1516,11 @@ int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp,
   }
   int launches = 0;
   int rc = GSOFA_OK;
-  if (!members.empty()) rc = run_batch_members(c, members, n, rp, ci, o, st, outs, &launches, transient);
+  if (!members.empty())
+    rc = run_batch_members(c, members, n, rp, ci, o, st, outs, &launches, transient, pool_entries);
   for (size_t j = 0; rc == GSOFA_OK && j < singles.size(); j++) {
     const int32_t k = singles[j];
-    rc = run_device(c, n[k], rp[k], ci[k], o, st, &outs[k]);
+    rc = run_device(c, n[k], rp[k], ci[k], o, st, &outs[k], pool_entries ? pool_entries[k] : 0);
     if (rc == GSOFA_OK) launches += outs[k].stats.kernel_launches;
   }
   if (rc != GSOFA_OK) {
@@ -1522,14 +1535,14 @@ int run_batch(Ctx* c, int32_t count, const int32_t* n, const int32_t* const* rp,
 
 // Served batches: one-off composition, pooled workspace, no graph (serve.cu).
 int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
-                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs) {
+                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs, const int64_t* pool_entries) {
   gsofa_options o;
   if (check_options(opt, &o) != GSOFA_OK) return GSOFA_E_INVAL;
   if (count <= 0) return count == 0 ? GSOFA_OK : GSOFA_E_INVAL;
   int err = GSOFA_OK;
   Ctx* c = get_ctx(&err);
   if (!c) return err;
-  return run_batch(c, count, n, rp, ci, o, st, outs, true);
+  return run_batch(c, count, n, rp, ci, o, st, outs, true, pool_entries);
 }
 
 int64_t global_slot_bytes(int32_t n) { return slot_bytes(((int64_t)n + 1023) / 1024 * 1024); }
@@ -1693,7 +1706,8 @@ int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     nnz = v;
   }
   if (tune) {
-    // time both frontier orders once for this shape and keep the faster
+    // time once per shape: breadth-first without and with the fill-first check
+    // (Section 4, "line 9.5"), and class order; keep the fastest
     const std::pair<int32_t, int64_t> key(n, nnz);
     int best = 0;
     {
@@ -1702,25 +1716,29 @@ int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       if (it != c->order_tuned.end()) best = it->second;
     }
     if (best == 0) {
-      float ms[3] = {0.f, 0.f, 0.f};
-      for (int ord = 1; ord <= 2; ord++) {
+      float ms[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int cand = 1; cand <= 3; cand++) {  // 1 breadth-first, 2 class order, 3 breadth-first + fill-first
         gsofa_options t = o;
-        t.frontier_order = ord;
+        t.frontier_order = cand == 2 ? 2 : 1;
+        t.fill_first = cand == 3 ? 1 : o.fill_first;
         t.collect_stats = 1;
         t.autotune = 0;
         for (int rep = 0; rep < 2; rep++) {  // the first run also sizes the row pool
           gsofa_result r;
           const int rc = run_device(c, n, d_rowptr, d_colidx, t, st, &r);
           if (rc) return rc;
-          ms[ord] = r.stats.ms_traverse;
+          ms[cand] = r.stats.ms_traverse;
           gsofa_free(&r);
         }
       }
-      best = ms[2] < ms[1] ? 2 : 1;
+      best = 1;
+      for (int cand = 2; cand <= 3; cand++)
+        if (ms[cand] < ms[best]) best = cand;
       std::lock_guard<std::mutex> lk(c->hmu);
       c->order_tuned[key] = best;
     }
-    o.frontier_order = best;
+    o.frontier_order = best == 2 ? 2 : 1;
+    if (best == 3) o.fill_first = 1;
   }
   return run_device(c, n, d_rowptr, d_colidx, o, st, out);
 }

@@ -157,8 +157,10 @@ cudaError_t launch_build_ell_batch(const MatDesc* mats, int32_t nmats, int64_t t
 cudaError_t launch_iota_desc(int32_t* out, int32_t hi, int32_t count, cudaStream_t st);
 
 // host helpers (api.cu)
+// Served batches: one-off composition, pooled workspace, no graph.  pool_entries
+// (per matrix, or null): the first row-pool size the caller charged for it.
 int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, const int32_t* const* ci,
-                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs);
+                    const gsofa_options* opt, cudaStream_t st, gsofa_result* outs, const int64_t* pool_entries);
 int device_sms();
 // Bytes of the global-tier slots a single-matrix call of order n would hold.
 int64_t global_tier_bytes(int32_t n, const gsofa_options* opts);

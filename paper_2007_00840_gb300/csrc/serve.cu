@@ -51,6 +51,7 @@ struct Request {
   const int32_t* h_ci = nullptr;
   int32_t* own = nullptr;           // server copy of a host CSR (rowptr then colidx)
   int64_t projected = 0;
+  int64_t est = 0;                  // projected nnz(L+U): the first row-pool size of its batch share
   int64_t budget = 0;               // space-budget mode: mem_budget_bytes of this request (0: server default)
   bool big = false;                 // runs alone (order above the on-chip limit)
   Charge* held = nullptr;           // result bytes charged until collected
@@ -94,12 +95,18 @@ struct gsofa_server {
 
 namespace {
 
+// Projected nnz(L+U) of a pattern: 64 per stored entry plus 16 per row, at most
+// the full triangle pair.
+int64_t projected_entries(int32_t n, int64_t nnz) {
+  int64_t est = 64 * nnz + 16 * (int64_t)n;
+  const int64_t full = (int64_t)n * ((int64_t)n + 1);
+  return est > full ? full : est;
+}
+
 int64_t projected_bytes(const gsofa_server* S, int32_t n, int64_t nnz, bool host_input) {
   const int64_t csr = host_input ? 4 * ((int64_t)n + 1) + 4 * nnz : 0;
   const int64_t rows = 96 * (int64_t)n;                        // per-row workspace, scans, row pointers
-  int64_t est = 64 * nnz + 16 * (int64_t)n;                    // projected nnz(L+U)
-  const int64_t full = (int64_t)n * ((int64_t)n + 1);
-  if (est > full) est = full;
+  const int64_t est = projected_entries(n, nnz);
   int64_t b = csr + rows + 8 * est + (1 << 20);                // row pool + L/U outputs
   if (n > S->smem_max_n) b += global_tier_bytes(n, &S->cfg.opts);  // global-tier slots, as a call would size them
   return b;
@@ -199,7 +206,7 @@ void worker_loop(gsofa_server* S, int slot) {
       const int32_t n1 = take[i]->n;
       const int32_t* rp1 = take[i]->rp;
       const int32_t* ci1 = take[i]->ci;
-      rcs[i] = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i]);
+      rcs[i] = batch_transient(1, &n1, &rp1, &ci1, &o, st, &outs[i], &take[i]->est);
       if (rcs[i] == GSOFA_OK) launches += outs[i].stats.kernel_launches;
     };
     if (small) {
@@ -208,9 +215,11 @@ void worker_loop(gsofa_server* S, int slot) {
       rps.clear();
       cis.clear();
       std::vector<int> in_batch;
+      std::vector<int64_t> pe;
       for (int i = 0; i < k; i++) {
         if (rcs[i] != GSOFA_OK) continue;
         in_batch.push_back(i);
+        pe.push_back(take[i]->est);
         ns.push_back(take[i]->n);
         rps.push_back(take[i]->rp);
         cis.push_back(take[i]->ci);
@@ -220,7 +229,8 @@ void worker_loop(gsofa_server* S, int slot) {
       if (!in_batch.empty()) {
         std::vector<gsofa_result> bo(in_batch.size());
         const int brc =
-            batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &bo_opts, st, bo.data());
+            batch_transient((int32_t)in_batch.size(), ns.data(), rps.data(), cis.data(), &bo_opts, st, bo.data(),
+                            pe.data());
         if (brc == GSOFA_OK) {
           launches += bo[0].stats.kernel_launches;  // the batch's total
           for (size_t j = 0; j < in_batch.size(); j++) outs[in_batch[j]] = bo[j];
@@ -395,6 +405,7 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
     r->h_ci = colidx;
   }
   if (r->nnz < 0) { delete r; return GSOFA_E_INVAL; }
+  r->est = projected_entries(n, r->nnz);
   r->projected = projected_bytes(S, n, r->nnz, !on_device);
   if (r->projected > S->cfg.mem_cap_bytes && n > S->smem_max_n) {
     // space-budget mode (the concurrent-source budget of Section 5, Eq. 1): run
