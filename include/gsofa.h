@@ -98,6 +98,13 @@ typedef struct gsofa_options {
     int32_t warps_per_sm;        /* class-ordered kernel on one matrix: resident warps (sources in flight)
                                     per SM, 0 automatic (32; 40 selects a 48-register build).  Batches
                                     choose theirs with autotune */
+    int32_t host_spill;          /* class-ordered kernel: keep each slot's log (level overflow and L row,
+                                    4 bytes per vertex) in pinned host memory the GPU reads directly,
+                                    and only the visited bitmaps (n/8 bytes per slot) in device memory:
+                                    the external frontier management of Section 6.  0 automatic (when
+                                    the slot budget cannot hold one whole slot in device memory), 1
+                                    always, -1 never (GSOFA_E_NOMEM instead).  Same result */
+    int32_t reserved;
 } gsofa_options;
 
 /* Per-call statistics.  Times, cycles and edges_scanned are filled when
@@ -224,8 +231,10 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
  * work overlaps on the GPU (opts.max_ctas can split the GPU between slots
  * instead).  A request whose slots alone would exceed the cap runs alone with
  * as many slots as the cap leaves room for (space-budget mode: fewer sources in
- * flight, same result); one that does not fit even with one slot is refused
- * with GSOFA_E_NOMEM.
+ * flight, same result); one that does not fit even with one slot runs with
+ * the slots' logs in host memory and only their visited bitmaps on the device
+ * (opts.host_spill >= 0), and is refused with GSOFA_E_NOMEM only when not even
+ * that fits.
  */
 typedef struct gsofa_server gsofa_server;
 

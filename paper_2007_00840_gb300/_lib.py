@@ -40,6 +40,8 @@ class gsofa_options(ctypes.Structure):
         ("schedule", ctypes.c_int32),
         ("team_sources", ctypes.c_int32),
         ("warps_per_sm", ctypes.c_int32),
+        ("host_spill", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -273,13 +273,19 @@ ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
   return k;
 }
 
+// Device bytes of a slot whose log lives in host memory: the visited bitmap
+// and its summary only.
+int64_t device_slot_bytes(int64_t cap) { return cap / 8 + cap / 256; }
+
 // Slots (one warp each) of the class-ordered kernel for order n: a full wave
-// of resident warps, within the budget, at most 4 per CTA allowed by max_ctas.
-int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o) {
+// of resident warps, within the budget (device bytes per slot: all of it, or
+// the bitmaps alone when the logs are in host memory), at most 4 per CTA
+// allowed by max_ctas.
+int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o, bool host_log = false) {
   const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
   const ClassCfg k = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
   int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * k.ctas_per_sm * CLASS_WARPS_PER_CTA;
-  const int64_t fit = global_budget(c, o) / slot_bytes(cap);
+  const int64_t fit = global_budget(c, o) / (host_log ? device_slot_bytes(cap) : slot_bytes(cap));
   if (slots > fit) slots = fit;
   if (o.max_ctas > 0 && slots > (int64_t)o.max_ctas * CLASS_WARPS_PER_CTA)
     slots = (int64_t)o.max_ctas * CLASS_WARPS_PER_CTA;
@@ -377,6 +383,7 @@ struct Plan {
   int async_sched = 0;    // shared tier: worklist schedule (the two lists form one ring >= S)
   ClassCfg cls;           // class-ordered kernel (sources S .. n-1)
   int32_t nbig = 0;       // of those, the largest expanded by four-warp CTA teams
+  bool host_log = false;  // the slots' logs in pinned host memory (Section 6 external frontier)
 };
 
 }  // namespace
@@ -463,7 +470,9 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
   }
   if (S < n) {
     // one warp per source (the largest: a CTA); a full wave of warps within the memory budget
-    const int64_t slots = global_slots(c, n, o);
+    int64_t slots = global_slots(c, n, o);
+    p->host_log = o.host_spill > 0 || (o.host_spill == 0 && slots < 1);
+    if (p->host_log) slots = global_slots(c, n, o, true);
     if (slots < 1) return GSOFA_E_NOMEM;
     p->cls = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
     p->glob_block = 32 * CLASS_WARPS_PER_CTA;
@@ -505,6 +514,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   if (in->warps_per_sm != 0 && (in->warps_per_sm < 4 || in->warps_per_sm > 48 || in->warps_per_sm % 4))
     return GSOFA_E_INVAL;
   o->warps_per_sm = in->warps_per_sm;
+  if (in->host_spill < -1 || in->host_spill > 1) return GSOFA_E_INVAL;
+  o->host_spill = in->host_spill;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -550,6 +561,11 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   bool have_global_lock = false;
   int nlaunch = 0;
   std::unique_lock<std::mutex> glk(c->gmu, std::defer_lock);
+  // host-log slots (plan.host_log): bitmaps from the pool, logs in mapped pinned host memory
+  uint32_t *hV = nullptr, *hVS = nullptr;
+  int32_t* hlog_dev = nullptr;
+  void* hlog_host = nullptr;
+  int64_t hcap = 0;
 
 #define CK(x)                        \
   do {                               \
@@ -594,7 +610,24 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   LK(launch_iota_desc(order, plan.S, plan.S, st));
   LK(launch_iota_desc(order + plan.S, n, n - plan.S, st));
 
-  if (plan.S < n) {
+  if (plan.S < n && plan.host_log) {
+    // the external frontier of Section 6: each slot's log (level overflow and L
+    // row) in host memory the kernel reads and writes directly; only the
+    // visited bitmaps take device memory
+    hcap = ((int64_t)n + 1023) / 1024 * 1024;
+    const size_t slots = (size_t)plan.glob_grid;
+    CK(palloc(c, &hV, (size_t)(hcap / 32) * slots, st));
+    CK(palloc(c, &hVS, (size_t)(hcap / 1024) * slots, st));
+    CK(cudaMemsetAsync(hV, 0, 4 * (size_t)(hcap / 32) * slots, st));
+    CK(cudaMemsetAsync(hVS, 0, 4 * (size_t)(hcap / 1024) * slots, st));
+    if (cudaHostAlloc(&hlog_host, 4 * (size_t)hcap * slots, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      hlog_host = nullptr;
+      rc = GSOFA_E_NOMEM;
+      goto fail;
+    }
+    CK(cudaHostGetDevicePointer((void**)&hlog_dev, hlog_host, 0));
+  } else if (plan.S < n) {
     glk.lock();
     have_global_lock = true;
     rc = ensure_slots(c, n, plan.glob_grid, st);
@@ -630,17 +663,17 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.order = order + plan.S;
       a.nsrc = n - plan.S;
       a.ell = ell;
-      a.g_V = c->g_V;
-      a.g_VS = c->g_VS;
-      a.g_log = c->g_log;
-      a.g_cap = c->g_cap;
+      a.g_V = plan.host_log ? hV : c->g_V;
+      a.g_VS = plan.host_log ? hVS : c->g_VS;
+      a.g_log = plan.host_log ? hlog_dev : c->g_log;
+      a.g_cap = plan.host_log ? hcap : c->g_cap;
       a.g_slots = plan.glob_grid;
       a.ct_qw = plan.cls.qw;
       a.ct_vwords = plan.cls.vwords;
       a.ct_nbig = plan.nbig;
       LK(launch_trav_class(a, (plan.glob_grid + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, plan.cls.vm,
                            plan.cls.warps_per_sm, st));
-      CK(cudaEventRecord(c->g_done, st));
+      if (!plan.host_log) CK(cudaEventRecord(c->g_done, st));
     }
     ev.rec(3, st);
     if (plan.S > 0) {
@@ -677,6 +710,13 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   }
   if (h->err & ERR_OVERFLOW) { rc = GSOFA_E_NOMEM; goto fail; }
   if (have_global_lock) { glk.unlock(); have_global_lock = false; }
+  if (plan.host_log) {
+    // the traversal is complete (its counters were read back)
+    if (hlog_host) cudaFreeHost(hlog_host);
+    hlog_host = nullptr;
+    pfree(hV, st);
+    pfree(hVS, st);
+  }
   {
     std::lock_guard<std::mutex> lk(c->hmu);
     c->pool_hint[n] = (long long)h->pool_cursor + ((long long)h->pool_cursor >> 4) + 1024;
@@ -744,6 +784,9 @@ fail:
   cudaGetLastError();
   if (have_global_lock) glk.unlock();
   wait_stream(st);
+  if (hlog_host) cudaFreeHost(hlog_host);
+  pfree(hV, st);
+  pfree(hVS, st);
   pfree(ctr, st);
   pfree(order, st);
   pfree(pool, st);
@@ -1546,6 +1589,8 @@ int batch_transient(int32_t count, const int32_t* n, const int32_t* const* rp, c
 }
 
 int64_t global_slot_bytes(int32_t n) { return slot_bytes(((int64_t)n + 1023) / 1024 * 1024); }
+
+int64_t global_device_slot_bytes(int32_t n) { return device_slot_bytes(((int64_t)n + 1023) / 1024 * 1024); }
 
 int32_t batch_class_slots(int32_t n_max) {
   int err = GSOFA_OK;

@@ -166,6 +166,8 @@ int device_sms();
 int64_t global_tier_bytes(int32_t n, const gsofa_options* opts);
 // Bytes of one global-tier slot for order n.
 int64_t global_slot_bytes(int32_t n);
+// Device bytes of one slot whose log lives in host memory (bitmaps only).
+int64_t global_device_slot_bytes(int32_t n);
 void detach_result_stream(gsofa_result* r);
 int32_t smem_tier_max_order();
 // Class-kernel slots an untuned batch of largest order n_max would use.

@@ -276,10 +276,6 @@ void worker_loop(gsofa_server* S, int slot) {
       ch->bytes += 16 * ((int64_t)o.n + 1) + 4 * (o.nnz_L + o.nnz_U) + 4 * (int64_t)o.n + 4 * ((int64_t)o.n_super + 1);
       ch->refs++;
     }
-    if (ch) {
-      S->in_use += ch->bytes;
-      if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
-    }
     for (int i = 0; i < k; i++) {
       Request* r = take[i];
       r->t_done = now;
@@ -298,6 +294,10 @@ void worker_loop(gsofa_server* S, int slot) {
       r->done = true;
       S->in_use -= r->projected;
       S->inflight--;
+    }
+    if (ch) {  // the results stay charged until collected
+      S->in_use += ch->bytes;
+      if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
     }
     S->t_last = now;
     admit(S);
@@ -416,6 +416,15 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
     if (slots >= 1) {
       r->budget = 2 * slots * one;  // the global tier takes half of mem_budget_bytes
       r->projected = base + slots * one;
+    } else if (S->cfg.opts.host_spill >= 0) {
+      // not even one whole slot: the slots' logs in host memory, their
+      // visited bitmaps alone on the device (Section 6 external frontier)
+      const int64_t dev = global_device_slot_bytes(n);
+      const int64_t hs = dev > 0 ? (S->cfg.mem_cap_bytes - base) / dev : 0;
+      if (hs >= 1) {
+        r->budget = 2 * hs * dev;
+        r->projected = base + hs * dev;
+      }
     }
   }
   if (r->projected > S->cfg.mem_cap_bytes) { delete r; return GSOFA_E_NOMEM; }
