@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "nd512": (-1, "grid2d_nd_512x512_p0.8"),  # the served stream's large request (first of its pool)
     "grid3d": (1, "grid3d_32^3_p0.6_extra1024"),
     "grid2d": (0, "grid2d_64x64_p0.7"),
     "nd1024": (2, "grid2d_nd_1024x1024_p0.8"),
@@ -86,6 +87,14 @@ def sum_over_ranks(x: float, world: int, device) -> float:
 
 
 L2_NOTE = "GPU arm: L2 flushed between steps (256 MB write)"
+
+
+def workload_matrix(k):
+    """The CSR of a single-matrix workload (k < 0: the 512^2 ND grid of the served pool)."""
+    import synth
+    if k < 0:
+        return synth.grid2d_nd(512, 0.8, seed=synth.config_seed(4), name="served_nd512_0")
+    return synth.config(k)
 
 
 def workload_config(name, A, nnz_lu, extra, world):
@@ -205,7 +214,7 @@ def run_reference(args, rank, world):
                           "the reference arm times single-matrix workloads; use --workload nd1024|grid3d|grid2d"}))
         return 0
     k, name = WORKLOADS[args.workload]
-    A = synth.config(k)
+    A = workload_matrix(k)
     extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
     for _ in range(args.warmup):
         cpu_baseline(A, 16, min_wall=0.0)
@@ -258,7 +267,7 @@ def main():
     if args.workload == "served":
         return run_served_bench(args, rank, world, local)
     k, name = WORKLOADS[args.workload]
-    A = synth.config(k)
+    A = workload_matrix(k)
     n = A.n
     dev = torch.device("cuda", local)
     rp = torch.from_numpy(A.rowptr).to(dev)
@@ -355,8 +364,8 @@ def main():
     traffic = stored_traffic(name) if not extra else None
 
     # the dominant traversal tier of this matrix
-    if stats0["ms_traverse_global"] > stats0["ms_traverse_smem"]:
-        kernel_name = "trav_global_kernel (class-ordered maxId traversal, one warp per source) + trav_smem_kernel"
+    if stats0["ms_traverse_global"] > stats0["ms_traverse_smem"]:  # the class-ordered kernel's time
+        kernel_name = "trav_class_kernel (class-ordered maxId traversal on a visited bitmap, one warp per source)"
     else:
         kernel_name = "trav_smem_kernel (maxId traversal, one CTA per source)"
     line = {
@@ -521,7 +530,7 @@ def run_batch_bench(args, rank, world, local):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "rows_per_s": world * args.steps * rows / t, "matrices_per_s": world * args.steps * len(mats) / t,
         "e2e": e2e, "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": ("trav_global_kernel (batched, class-ordered, one warp per source)"
+        "roofline": {"bound": "hbm", "kernel": ("trav_class_kernel (batched, class-ordered, one warp per source)"
                                                 if tuned and tuned["kernel"] == "warp_per_source_class"
                                                 else "trav_smem_kernel (batched, one CTA per source)"),
                      "achieved": alg / t_trav / 1e9,

@@ -104,6 +104,13 @@ typedef struct gsofa_options {
                                     the external frontier management of Section 6.  0 automatic (when
                                     the slot budget cannot hold one whole slot in device memory), 1
                                     always, -1 never (GSOFA_E_NOMEM instead).  Same result */
+    int32_t clean_heads;         /* class-ordered kernel: retire runs of pending classes whose heads reach
+                                    nothing new (every neighbour already reached) together, up to 32 per
+                                    warp-wide check, instead of one class at a time.  0 automatic (on
+                                    where the visited bitmaps are in global memory, off where they are
+                                    in shared memory), 1 on (after a check that retires nothing, the next
+                                    1, 3, 7, 15 or 31 classes go one at a time), 2 a check before every
+                                    class, -1 off.  Same result */
     int32_t reserved;
 } gsofa_options;
 

@@ -41,6 +41,7 @@ class gsofa_options(ctypes.Structure):
         ("team_sources", ctypes.c_int32),
         ("warps_per_sm", ctypes.c_int32),
         ("host_spill", ctypes.c_int32),
+        ("clean_heads", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
 

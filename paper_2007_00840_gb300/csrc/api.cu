@@ -251,6 +251,16 @@ struct ClassCfg {
 
 constexpr int CLASS_VM_SMEM = 0, CLASS_VM_GLOBAL = 1;
 
+// Device setting of the clean-head gathers for option clean_heads: automatic
+// (0) gathers, with back-off, only where the visited bitmaps are in global
+// memory (there a class head costs dependent L2 round trips; with shared
+// bitmaps one class at a time was faster on every workload measured).
+int clean_heads_mode(int opt, int vm) {
+  if (opt < 0) return -1;
+  if (opt == 0) return vm == CLASS_VM_GLOBAL ? 0 : -1;
+  return opt == 1 ? 0 : 1;
+}
+
 ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
   (void)c;
   ClassCfg k;
@@ -269,6 +279,7 @@ ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
     k.vwords = words;
     const int occ = trav_class_occupancy(CLASS_VM_GLOBAL, warps_per_sm, k.vwords, k.qw);
     k.ctas_per_sm = occ < want ? occ : want;
+
   }
   return k;
 }
@@ -516,6 +527,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->warps_per_sm = in->warps_per_sm;
   if (in->host_spill < -1 || in->host_spill > 1) return GSOFA_E_INVAL;
   o->host_spill = in->host_spill;
+  if (in->clean_heads < -1 || in->clean_heads > 2) return GSOFA_E_INVAL;
+  o->clean_heads = in->clean_heads;
   o->autotune = in->autotune ? 1 : 0;
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
@@ -555,6 +568,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   int32_t* spill = nullptr;
   int64_t spill_cap = 0;
   int4* ell = nullptr;
+  int4* ellw = nullptr;  // class kernel, orders past 32,768 (16-bit offsets may not reach)
   DevCounters* h = pinned_counters();
   Plan plan;
   long long pool_cap = 0;
@@ -605,7 +619,10 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     spill_cap = plan.S > plan.list_cap ? plan.S - plan.list_cap : 1;
     CK(palloc(c, &spill, (size_t)plan.smem_grid * 2 * (size_t)spill_cap, st));
   }
-  if (n > 0 && (o.expand_mode == 0 || o.expand_mode == 3)) CK(palloc(c, &ell, (size_t)n, st));
+  if (n > 0 && (o.expand_mode == 0 || o.expand_mode == 3)) {
+    if (plan.S < n && n > 32768) CK(palloc(c, &ellw, 2 * (size_t)n, st));
+    if (plan.S > 0 || !ellw) CK(palloc(c, &ell, (size_t)n, st));
+  }
   // order: shared tier [S-1 .. 0] then global tier [n-1 .. S] (largest source first)
   LK(launch_iota_desc(order, plan.S, plan.S, st));
   LK(launch_iota_desc(order + plan.S, n, n - plan.S, st));
@@ -644,6 +661,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       ev.rec(1, st);
     }
     if (ell && attempt == 0) LK(launch_build_ell(n, d_rowptr, d_colidx, ell, ctr, st));
+    if (ellw && attempt == 0) LK(launch_build_ellw(n, d_rowptr, d_colidx, ellw, ctr, st));
     TravArgs a;
     std::memset(&a, 0, sizeof(a));
     a.n = n;
@@ -663,6 +681,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.order = order + plan.S;
       a.nsrc = n - plan.S;
       a.ell = ell;
+      a.ellw = ellw;
       a.g_V = plan.host_log ? hV : c->g_V;
       a.g_VS = plan.host_log ? hVS : c->g_VS;
       a.g_log = plan.host_log ? hlog_dev : c->g_log;
@@ -671,6 +690,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
       a.ct_qw = plan.cls.qw;
       a.ct_vwords = plan.cls.vwords;
       a.ct_nbig = plan.nbig;
+      a.ct_heads = clean_heads_mode(o.clean_heads, plan.cls.vm);
       LK(launch_trav_class(a, (plan.glob_grid + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, plan.cls.vm,
                            plan.cls.warps_per_sm, st));
       if (!plan.host_log) CK(cudaEventRecord(c->g_done, st));
@@ -763,6 +783,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
   pfree(flag_pos, st);
   pfree(spill, st);
   pfree(ell, st);
+  pfree(ellw, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   scan_tmp = nullptr;
 
@@ -797,6 +818,7 @@ fail:
   pfree(flag_pos, st);
   pfree(spill, st);
   pfree(ell, st);
+  pfree(ellw, st);
   if (scan_tmp) cudaFreeAsync(scan_tmp, st);
   {
     const int32_t det = out->err_detail;
@@ -1049,6 +1071,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
     a.ct_qw = p.c_cfg.qw;
     a.ct_vwords = p.c_cfg.vwords;
     a.ct_nbig = 0;
+    a.ct_heads = clean_heads_mode(o.clean_heads, p.c_cfg.vm);
     if ((e = launch_trav_class(a, (p.shape.slots + CLASS_WARPS_PER_CTA - 1) / CLASS_WARPS_PER_CTA, p.c_cfg.vm,
                                p.c_cfg.warps_per_sm, st)) != cudaSuccess)
       return e;
@@ -1494,7 +1517,7 @@ int run_batch_members(Ctx* c, const std::vector<int32_t>& members, const int32_t
   sig = mix64(sig, ((uint64_t)o.collect_stats << 32) ^ (uint64_t)o.max_ctas);
   sig = mix64(sig, ((uint64_t)o.frontier_order << 48) ^ ((uint64_t)o.expand_mode << 32) ^
                        ((uint64_t)o.label_bits << 16) ^ (uint64_t)o.autotune);
-  sig = mix64(sig, (uint64_t)(uint32_t)o.team_sources);
+  sig = mix64(sig, ((uint64_t)(uint32_t)o.clean_heads << 32) ^ (uint64_t)(uint32_t)o.team_sources);
   std::unique_lock<std::mutex> lk(bc.mu);  // cached plans are used by one call at a time
   load_tune_file(bc);
   BatchPlan* p = nullptr;

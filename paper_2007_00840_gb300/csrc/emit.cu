@@ -580,6 +580,34 @@ __global__ void build_ell_kernel(int32_t n, const int32_t* __restrict__ rowptr, 
     ell[v] = ell_record(rowptr, colidx, n, v);
 }
 
+// Wide record of row v: up to 8 off-diagonal columns as int32 (unused slots v).
+__device__ void ellw_record(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int32_t n,
+                            int32_t v, int4* __restrict__ out) {
+  const int rb = rowptr[v], re = rowptr[v + 1];
+  int c[8] = {v, v, v, v, v, v, v, v};
+  int k = 0;
+  bool fits = true;
+  for (int e = rb; e < re; e++) {
+    const int w = colidx[e];
+    if (w == v) continue;
+    if (k == 8 || w < 0 || w >= n) { fits = false; break; }
+    c[k++] = w;
+  }
+  if (!fits) {
+    c[0] = -1;
+    for (int q = 1; q < 8; q++) c[q] = v;
+  }
+  out[0] = make_int4(c[0], c[1], c[2], c[3]);
+  out[1] = make_int4(c[4], c[5], c[6], c[7]);
+}
+
+__global__ void build_ellw_kernel(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                  int4* __restrict__ ellw, DevCounters* ctr) {
+  if (input_error(ctr)) return;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    ellw_record(rowptr, colidx, n, (int32_t)v, ellw + 2 * v);
+}
+
 // Records of every row of a batch, indexed by the row's global index (row_base + v).
 __global__ void build_ell_batch_kernel(const MatDesc* __restrict__ mats, int32_t nmats, long long total_rows,
                                        int4* __restrict__ ell, DevCounters* ctr) {
@@ -608,6 +636,15 @@ cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* co
   long long grid = ((long long)n + block - 1) / block;
   if (grid > 8192) grid = 8192;
   build_ell_kernel<<<(int)grid, block, 0, st>>>(n, rowptr, colidx, ell, ctr);
+  return cudaGetLastError();
+}
+cudaError_t launch_build_ellw(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ellw, DevCounters* ctr,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int block = 256;
+  long long grid = ((long long)n + block - 1) / block;
+  if (grid > 8192) grid = 8192;
+  build_ellw_kernel<<<(int)grid, block, 0, st>>>(n, rowptr, colidx, ellw, ctr);
   return cudaGetLastError();
 }
 }  // namespace gsofa

@@ -99,6 +99,8 @@ struct TravArgs {
   int32_t ct_qw;                      // shared queue entries per warp and level parity
   int32_t ct_vwords;                  // shared V: words per warp (>= ceil(n/32))
   int32_t ct_nbig;                    // leading work items processed by four-warp CTA teams
+  int32_t ct_heads;                   // clean-head gathers: -1 off, 0 adaptive, 1 before every class
+  const int4* ellw;                   // class kernel: 32-bit column records, row v at ellw[2v..2v+1] (null: ell)
 };
 
 // ---- launchers (return cudaGetLastError())
@@ -150,6 +152,11 @@ cudaError_t launch_scatter_starts(int32_t n, const int32_t* flags, const int64_t
                                   int32_t* super_start, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t* p, int64_t count, int32_t v, cudaStream_t st);
 cudaError_t launch_init_counters(DevCounters* c, cudaStream_t st);
+// Wide records for the class kernel: the (at most 8) off-diagonal columns of
+// row v as int32 in ellw[2v], ellw[2v+1], empty slots holding v itself; rows
+// with more entries (or a column out of range) have -1 in slot 0.
+cudaError_t launch_build_ellw(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ellw, DevCounters* ctr,
+                              cudaStream_t st);
 cudaError_t launch_build_ell(int32_t n, const int32_t* rowptr, const int32_t* colidx, int4* ell, DevCounters* ctr,
                              cudaStream_t st);
 cudaError_t launch_build_ell_batch(const MatDesc* mats, int32_t nmats, int64_t total_rows, int4* ell,

@@ -245,9 +245,125 @@ struct Src {
   const int32_t* __restrict__ rowptr;
   const int32_t* __restrict__ colidx;
   const int4* __restrict__ ell;  // records of this matrix (row v at ell[v]) or null
+  const int4* __restrict__ ellw; // wide records (row v at ellw[2v], ellw[2v+1]) or null
   long long rowb;                // row offset in the per-row arrays (batch)
   int mi;
 };
+
+// Clean class heads.  A pending class t whose head has every neighbour
+// (other than s) in V already changes nothing when expanded: no member, no
+// new fill, no new U entry.  Taken in increasing order, each such class
+// leaves V as it found it, so a run of them can be decided together: the
+// warp gathers the (up to 32) smallest pending classes t_0 < t_1 < ... from
+// t0 on, reads their heads' neighbours' bits, and retires the longest prefix
+// of clean heads at once (appended to L(s,:)).  The first class that is not
+// clean, if any, is returned in tnext and expanded as usual; the classes
+// after it stay pending.  Returns the number retired; last = the largest
+// class gathered (when every gathered class was clean, the search resumes
+// above it).  Warp-wide; the scratch is the team's even-level queue, free
+// between classes.
+template <int VM>
+__device__ int retire_clean(const TravArgs& a, const Src& sc, const Team& tm, int t0, int nL, int lane, int& tnext,
+                            int& last, unsigned long long& n_exp, unsigned long long& n_edge) {
+  const int s = sc.s;
+  const int K = tm.qcap < 32 ? tm.qcap : 32;
+  // gather: lane l reads word (t0 >> 5) + l; set bits in [t0, s) ranked by a warp scan
+  const int wl = (t0 >> 5) + lane;
+  uint32_t m = 0u;
+  if ((wl << 5) < s) {
+    if constexpr (VM == VM_SMEM) m = tm.V[wl];
+    else m = ld_cg(tm.V + wl);
+    if (lane == 0) m &= 0xFFFFFFFFu << (t0 & 31);
+    const int hi = s - (wl << 5);
+    if (hi < 32) m &= (1u << hi) - 1u;
+  }
+  const int c = __popc(m);
+  int inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += x;
+  }
+  const int total = __shfl_sync(FULL, inc, 31);
+  int pos = inc - c;
+  while (m && pos < K) {
+    const int b = __ffs(m) - 1;
+    m &= m - 1;
+    tm.qa[pos++] = (wl << 5) + b;
+  }
+  __syncwarp();
+  const int cnt = total < K ? total : K;  // >= 1: t0 is pending
+  const int tj = lane < cnt ? tm.qa[lane] : -1;
+  __syncwarp();
+  // check: every neighbour of t_j (CSR rows of more than 8 entries count as not clean)
+  bool clean = false;
+  int deg = 0;
+  if (tj >= 0) {
+    int wv[8];
+    int nw = 0;
+    bool csr = sc.ell == nullptr && sc.ellw == nullptr;
+    if (sc.ellw) {
+      const int4 r0 = __ldg(sc.ellw + 2 * (size_t)tj), r1 = __ldg(sc.ellw + 2 * (size_t)tj + 1);
+      wv[0] = r0.x; wv[1] = r0.y; wv[2] = r0.z; wv[3] = r0.w;
+      wv[4] = r1.x; wv[5] = r1.y; wv[6] = r1.z; wv[7] = r1.w;
+      if (wv[0] < 0) csr = true;  // sentinel
+      else nw = 8;                // empty slots hold t_j itself
+    } else if (!csr) {
+      const int4 r = __ldg(sc.ell + tj);
+      const uint32_t h[4] = {(uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, (uint32_t)r.w};
+      if ((h[0] & 0xFFFFu) == 0x8000u) {
+        csr = true;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int off = (int)(short)((q & 1) ? (h[q >> 1] >> 16) : (h[q >> 1] & 0xFFFFu));
+          wv[q] = tj + off;  // offset 0 (empty slot): w == t_j, skipped below
+        }
+        nw = 8;
+      }
+    }
+    clean = true;
+    if (csr) {
+      const int rb = __ldg(sc.rowptr + tj), re = __ldg(sc.rowptr + tj + 1);
+      if (re - rb > 8) {
+        clean = false;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; q++) wv[q] = q < re - rb ? __ldg(sc.colidx + rb + q) : tj;
+        nw = 8;
+      }
+    }
+    if (clean) {
+      uint32_t wd[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int w = wv[q];
+        wd[q] = 0xFFFFFFFFu;
+        if (q < nw && w != tj && w != s) {
+          if ((unsigned)w >= (unsigned)sc.n) wd[q] = 0u;  // left to the expansion, which flags it
+          else if constexpr (VM == VM_SMEM) wd[q] = tm.V[w >> 5];
+          else wd[q] = ld_cg(tm.V + (w >> 5));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (!((wd[q] >> (wv[q] & 31)) & 1u)) clean = false;
+    }
+    if (a.collect_stats) deg = __ldg(sc.rowptr + tj + 1) - __ldg(sc.rowptr + tj);
+  }
+  const unsigned dirty = __ballot_sync(FULL, tj >= 0 && !clean);
+  const int k = dirty ? __ffs(dirty) - 1 : cnt;
+  if (lane < k) {
+    *l_slot(tm, nL + lane) = tj;
+    if (a.collect_stats) {
+      n_exp++;
+      n_edge += (unsigned long long)deg;
+    }
+  }
+  tnext = k < cnt ? __shfl_sync(FULL, tj, k & 31) : -1;
+  last = __shfl_sync(FULL, tj, (cnt - 1) & 31);
+  return k;
+}
 
 }  // namespace
 
@@ -321,43 +437,72 @@ __device__ void expand_level(const TravArgs& a, const Src& sc, const Team& tm, C
     int wv[K];
     bool fb = false;
     unsigned em = 0u;
-    uint32_t h[(K + 1) / 2];
-#pragma unroll
-    for (int q = 0; q < (K + 1) / 2; q++) h[q] = 0u;
-    if (v >= 0) {
-      if (sc.ell) {
-        if constexpr (K == 8) {
-          const int4 r = __ldg(sc.ell + v);
-          h[0] = (uint32_t)r.x; h[1] = (uint32_t)r.y; h[2] = (uint32_t)r.z; h[3] = (uint32_t)r.w;
-        } else if constexpr (K == 4) {
-          const int2 r = __ldg((const int2*)(sc.ell + v) + sub);
-          h[0] = (uint32_t)r.x; h[1] = (uint32_t)r.y;
-        } else if constexpr (K == 2) {
-          h[0] = (uint32_t)__ldg((const int*)(sc.ell + v) + sub);
-        } else {
-          h[0] = (uint32_t)(unsigned short)__ldg((const short*)(sc.ell + v) + sub);
-        }
-        fb = sub == 0 && (h[0] & 0xFFFFu) == 0x8000u;  // sentinel: the row is read from the CSR
-        if (fb) h[0] = 0u;
-      } else {
-        fb = sub == 0;
-      }
-      if (a.collect_stats && sub == 0) {
-        n_exp++;
-        n_edge += (unsigned long long)(__ldg(sc.rowptr + v + 1) - __ldg(sc.rowptr + v));
-      }
-    }
-    // empty slots (offset 0) and lanes without a vertex give w == v: skipped
+    bool hi4 = false;  // K == 8: slots 4-7 hold neighbours (records are packed)
+    // empty slots and lanes without a vertex give w == v (0 for no vertex): skipped
     const int vv = v < 0 ? 0 : v;
+    if (sc.ellw) {
 #pragma unroll
-    for (int q = 0; q < K; q++) {
-      const uint32_t half = (q & 1) ? (h[q >> 1] >> 16) : (h[q >> 1] & 0xFFFFu);
-      wv[q] = vv + (int)(short)half;
+      for (int q = 0; q < K; q++) wv[q] = vv;
+      if (v >= 0) {
+        const int4* rec = sc.ellw + 2 * (size_t)v;
+        if constexpr (K == 8) {
+          const int4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+          wv[0] = r0.x; wv[1] = r0.y; wv[2] = r0.z; wv[3] = r0.w;
+          wv[4] = r1.x; wv[5] = r1.y; wv[6] = r1.z; wv[7] = r1.w;
+        } else if constexpr (K == 4) {
+          const int4 r = __ldg(rec + sub);
+          wv[0] = r.x; wv[1] = r.y; wv[2] = r.z; wv[3] = r.w;
+        } else if constexpr (K == 2) {
+          const int2 r = __ldg((const int2*)rec + sub);
+          wv[0] = r.x; wv[1] = r.y;
+        } else {
+          wv[0] = __ldg((const int*)rec + sub);
+        }
+        fb = sub == 0 && wv[0] < 0;  // sentinel: the row is read from the CSR
+        if (fb) wv[0] = vv;
+        if constexpr (K == 8) hi4 = wv[4] != vv;
+        if (a.collect_stats && sub == 0) {
+          n_exp++;
+          n_edge += (unsigned long long)(__ldg(sc.rowptr + v + 1) - __ldg(sc.rowptr + v));
+        }
+      }
+    } else {
+      uint32_t h[(K + 1) / 2];
+#pragma unroll
+      for (int q = 0; q < (K + 1) / 2; q++) h[q] = 0u;
+      if (v >= 0) {
+        if (sc.ell) {
+          if constexpr (K == 8) {
+            const int4 r = __ldg(sc.ell + v);
+            h[0] = (uint32_t)r.x; h[1] = (uint32_t)r.y; h[2] = (uint32_t)r.z; h[3] = (uint32_t)r.w;
+          } else if constexpr (K == 4) {
+            const int2 r = __ldg((const int2*)(sc.ell + v) + sub);
+            h[0] = (uint32_t)r.x; h[1] = (uint32_t)r.y;
+          } else if constexpr (K == 2) {
+            h[0] = (uint32_t)__ldg((const int*)(sc.ell + v) + sub);
+          } else {
+            h[0] = (uint32_t)(unsigned short)__ldg((const short*)(sc.ell + v) + sub);
+          }
+          fb = sub == 0 && (h[0] & 0xFFFFu) == 0x8000u;  // sentinel: the row is read from the CSR
+          if (fb) h[0] = 0u;
+        } else {
+          fb = sub == 0;
+        }
+        if (a.collect_stats && sub == 0) {
+          n_exp++;
+          n_edge += (unsigned long long)(__ldg(sc.rowptr + v + 1) - __ldg(sc.rowptr + v));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < K; q++) {
+        const uint32_t half = (q & 1) ? (h[q >> 1] >> 16) : (h[q >> 1] & 0xFFFFu);
+        wv[q] = vv + (int)(short)half;
+      }
+      if constexpr (K == 8) hi4 = (h[2] | h[3]) != 0u;
     }
     if constexpr (K == 8) {
-      // records are packed, so slots 4-7 are empty for rows of up to 4 neighbours
       relax_group<VM, 8, 0, 4>(tm, wv, vv, sc.s, t, em, st);
-      if (__any_sync(FULL, (h[2] | h[3]) != 0u)) relax_group<VM, 8, 4, 4>(tm, wv, vv, sc.s, t, em, st);
+      if (__any_sync(FULL, hi4)) relax_group<VM, 8, 4, 4>(tm, wv, vv, sc.s, t, em, st);
     } else {
       relax_group<VM, K, 0, K>(tm, wv, vv, sc.s, t, em, st);
     }
@@ -586,6 +731,7 @@ __device__ __forceinline__ Src source_of(const TravArgs& a, int k) {
   sc.rowptr = a.rowptr;
   sc.colidx = a.colidx;
   sc.ell = a.ell;
+  sc.ellw = a.mats ? nullptr : a.ellw;
   sc.rowb = 0;
   sc.mi = 0;
   if (a.mats) {  // batch: smallest source index s with item_start[s] <= k, then the matrix
@@ -612,6 +758,34 @@ struct Counts {
   unsigned long long n_exp = 0, n_edge = 0, n_lev = 0;
   int bad = 0;
 };
+
+// The next class to expand from cursor on, retiring runs of clean heads on
+// the way (ct_heads >= 0); -1 when no class is pending.  Adaptive mode
+// (ct_heads == 0): after a gather whose first class was not clean, the next
+// 1, 3, 7, 15 or 31 classes are taken one by one before the next gather.
+template <int VM>
+__device__ int next_expand(const TravArgs& a, const Src& sc, const Team& tm, int& cursor, int& nL, int& skip,
+                           int& fails, int lane, Counts& cn) {
+  for (;;) {
+    const int t = next_class<VM>(tm, cursor, sc.s, lane);
+    if (t < 0 || a.ct_heads < 0) return t;
+    if (skip > 0) {
+      skip--;
+      return t;
+    }
+    int tn = -1, last = t;
+    const int k = retire_clean<VM>(a, sc, tm, t, nL, lane, tn, last, cn.n_exp, cn.n_edge);
+    nL += k;
+    if (k == 0 && a.ct_heads == 0) {
+      fails = fails < 5 ? fails + 1 : 5;
+      skip = (1 << fails) - 1;
+    } else if (k > 0) {
+      fails = 0;
+    }
+    if (tn >= 0) return tn;
+    cursor = last + 1;
+  }
+}
 
 // One source from seeds to a cleared V.  TEAM: the whole CTA (warp 0 searches
 // classes, expands their heads and emits), else the calling warp.
@@ -643,6 +817,7 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
   }
 
   int cursor = 0, nL = 0;
+  int skip = 0, fails = 0;  // clean-head gathers (leader only)
   int level = 0;  // team mode: running level index (queues and counters rotate with it)
   for (;;) {
     int t;
@@ -651,7 +826,7 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       // level; the counter it fills and the one it zeroes are not the one the
       // other warps may still be reading (the last level's zero length)
       if (leader) {
-        t = next_class<VM>(tm, cursor, s, lane);
+        t = next_expand<VM>(a, sc, tm, cursor, nL, skip, fails, lane, cn);
         int nq = 0;
         if (t >= 0) {
           if (lane == 0) *l_slot(tm, nL) = t;
@@ -683,7 +858,7 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
         __syncthreads();
       }
     } else {
-      t = next_class<VM>(tm, cursor, s, lane);
+      t = next_expand<VM>(a, sc, tm, cursor, nL, skip, fails, lane, cn);
       if (t < 0) break;
       cursor = t + 1;
       if (lane == 0) *l_slot(tm, nL) = t;

@@ -59,6 +59,7 @@ int main(void) {
          offsetof(gsofa_server_config, opts), offsetof(gsofa_server_stats, span_s));
   printf("%zu %zu %zu %zu\n", offsetof(gsofa_options, max_ctas), offsetof(gsofa_options, team_sources),
          offsetof(gsofa_options, label_bits), offsetof(gsofa_options, schedule));
+  printf("%zu\n", offsetof(gsofa_options, clean_heads));
   return 0;
 }
 """
@@ -75,6 +76,7 @@ int main(void) {
     C, T = _lib.gsofa_server_config, _lib.gsofa_server_stats
     assert vals[9:13] == [ctypes.sizeof(C), ctypes.sizeof(T), C.opts.offset, T.span_s.offset]
     assert vals[13:17] == [O.max_ctas.offset, O.team_sources.offset, O.label_bits.offset, O.schedule.offset]
+    assert vals[17] == O.clean_heads.offset
 
 
 def test_defaults_and_errors_without_gpu():

@@ -106,6 +106,61 @@ def test_worklist_schedule_exact():
     assert_same(run_gpu(A, schedule=2), oracle_full(A, nthreads=16))
 
 
+def _class_order_case_list():
+    n = 300
+    r = np.concatenate([np.zeros(n), np.arange(n), np.arange(n)])
+    c = np.concatenate([np.arange(n), np.zeros(n), np.arange(n)])
+    star = synth._csr_from_pairs(n, r, c, "star0")
+    r = np.concatenate([np.arange(1, n), np.arange(n)])
+    c = np.concatenate([np.arange(0, n - 1), np.arange(n)])
+    chain = synth._csr_from_pairs(n, r, c, "chain_down")
+    rng = np.random.default_rng(5)
+    rr, cc = [], []
+    for i in range(400):
+        k = 60 if i % 37 == 0 else (9 if i % 5 == 0 else 3)   # rows past one 8-entry record
+        cols = rng.choice(400, size=k, replace=False)
+        rr += [i] * k
+        cc += cols.tolist()
+    bigdeg = synth._csr_from_pairs(400, np.array(rr), np.array(cc), "bigdeg")
+    return [synth.grid2d_nd(60, 0.8, seed=23, leaf=16), synth.grid2d_nd(200, 0.8, seed=3),
+            synth.random_pattern(300, 0.02, seed=24, diag=False), synth.random_pattern(40, 0.3, seed=5),
+            star, chain, bigdeg, synth.grid2d(40, 0.7, seed=21), synth.banded(2500, 30, seed=22),
+            synth.banded(40000, 30, seed=25),   # past 32,768 rows: 32-bit records, rows past 8 entries
+            load_paper_example()[0]]
+
+
+def _class_order_run(A, **opt):
+    import torch
+    import paper_2007_00840_gb300 as gs
+    rp, ci = to_device(A)
+    r = gs.symbolic_device(rp, ci, opts=gs.options(frontier_order=2, collect_stats=1, **opt))
+    torch.cuda.synchronize()
+    return r.stats, r.to_host()
+
+
+def test_clean_head_retirement():
+    """Class order with runs of clean class heads (heads whose neighbours are all
+    reached already) retired together: off, adaptive, before every class, with
+    and CTA teams.  Same rows as the oracle, and class order expands every reached
+    vertex below the source exactly once, so the expansion and scanned-entry counts
+    equal the oracle's minimum-work counts (Dijkstra order, Section 8)."""
+    for A in _class_order_case_list():
+        o = oracle_full(A)
+        for opt in ({"clean_heads": -1}, {"clean_heads": 0}, {"clean_heads": 1}, {"clean_heads": 2},
+                    {"clean_heads": 2, "team_sources": 64}, {"clean_heads": 1, "team_sources": 8}):
+            st, h = _class_order_run(A, **opt)
+            assert_same(h, o), (A.name, opt)
+            assert st["vertices_expanded"] == int(o["vscan"].sum()), (A.name, opt)
+            assert st["edges_scanned"] == int(o["escan"].sum()), (A.name, opt)
+    # bitmaps in global memory (orders past the shared-memory bitmap limit)
+    A = synth.grid2d_nd(400, 0.8, seed=3)          # n = 160,000
+    o = oracle_full_cached(("nd400", 3), A)
+    for opt in ({"clean_heads": -1}, {"clean_heads": 0}, {"clean_heads": 2}, {"clean_heads": 2, "team_sources": 256}):
+        st, h = _class_order_run(A, **opt)
+        assert_same(h, o), opt
+        assert st["vertices_expanded"] == int(o["vscan"].sum()), opt
+
+
 def test_empty_matrix():
     A = synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), "empty")
     h = run_gpu(A)
