@@ -274,7 +274,7 @@ def main():
     ci = torch.from_numpy(A.colidx).to(dev)
     stream = torch.cuda.current_stream(dev)
     extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
-    opts = gs.options(collect_stats=1, **extra)
+    opts = gs.options(collect_stats=2, **extra)  # phase times; the work counters come from one extra call
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
 
     def barrier():
@@ -309,6 +309,11 @@ def main():
     barrier()
     wall = time.perf_counter() - w0
     clocks = sampler.stop() if sampler else None
+    # work counters (expanded vertices, scanned entries) from one untimed call that records them
+    r = gs.symbolic_device(rp, ci, opts=gs.options(collect_stats=1, **extra), stream=stream)
+    work = {k2: r.stats[k2] for k2 in ("vertices_expanded", "edges_scanned")}
+    del r
+    torch.cuda.synchronize(dev)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     t_dev = sum(step_ms) / 1000.0
     t_dev = max_over_ranks(t_dev, world, dev)
@@ -383,9 +388,8 @@ def main():
                      "peak_source": f"{peak_src} (copy bandwidth, burst)", "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg, "ms_per_launch": t_trav * 1000.0},
         "clocks": clocks,
-        "stats": {k2: stats0[k2] for k2 in ("ms_validate", "ms_traverse", "ms_traverse_smem", "ms_traverse_global",
-                                            "ms_supernode", "ms_emit", "ms_total",
-                                            "vertices_expanded", "edges_scanned", "pool_retries")},
+        "stats": {**{k2: stats0[k2] for k2 in ("ms_validate", "ms_traverse", "ms_traverse_smem", "ms_traverse_global",
+                                               "ms_supernode", "ms_emit", "ms_total", "pool_retries")}, **work},
         "oracle_min_work": {"vscan": int(orc["vscan"].sum()), "escan": int(orc["escan"].sum())},
     }
     if not args.no_cpu_baseline:
@@ -441,7 +445,7 @@ def run_batch_bench(args, rank, world, local):
     dmats = [(torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev)) for A in mats]
     rows = sum(A.n for A in mats)
     extra = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.opt}
-    opts = gs.options(**{"collect_stats": 1, "autotune": 1, **extra})
+    opts = gs.options(**{"collect_stats": 2, "autotune": 1, **extra})
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     import tempfile

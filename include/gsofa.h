@@ -63,7 +63,8 @@ typedef struct gsofa_options {
                                     the device memory free at first use, at most 96 GiB) */
     int32_t fill_first;          /* 1: skip lowering the maxId of a vertex already known to be a fill
                                     (the optional "line 9.5" of Section 4); same result */
-    int32_t collect_stats;       /* 1: record per-phase CUDA-event times and work counters */
+    int32_t collect_stats;       /* 1: record per-phase CUDA-event times and work counters (expanded vertices,
+                                    scanned entries: extra loads in the traversal), 2: the times only */
     int32_t validate;            /* 0 or 1: check the CSR on the device first (default 1); 2: skip */
     int32_t autotune;            /* 1 = time candidates once and keep the fastest: gsofa_batch per batch shape
                                     (kernel, block size, CTAs or warps per SM, frontier list capacity,
@@ -114,9 +115,10 @@ typedef struct gsofa_options {
     int32_t reserved;
 } gsofa_options;
 
-/* Per-call statistics.  Times, cycles and edges_scanned are filled when
- * options.collect_stats == 1; kernel_launches, pool_retries, levels and the
- * shared-memory tier's vertices_expanded always. */
+/* Per-call statistics.  Times are filled when options.collect_stats is 1 or 2,
+ * cycles, edges_scanned and the class-ordered kernel's vertices_expanded when
+ * it is 1; kernel_launches, pool_retries, levels and the shared-memory tier's
+ * vertices_expanded always. */
 typedef struct gsofa_stats {
     float ms_validate, ms_traverse, ms_emit, ms_supernode, ms_total;
     float ms_traverse_smem, ms_traverse_global;
@@ -225,16 +227,17 @@ int gsofa_row_counts_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *
  * that factors incoming sparsity patterns with continuous batching.
  * Requests are admitted in arrival order while the server's device memory fits
  * under mem_cap_bytes: each admitted request is charged its projected bytes
- * (CSR copy, per-row workspace, row pool and outputs, class-kernel slots of
- * large orders), each running batch the class-kernel slots it uses (fewer
- * slots when the cap leaves less room), and each completed result its size
- * until the caller collects it (a batch's results share one block, released
- * with the last of them; uncollected results therefore hold admission back).
+ * (CSR copy, per-row workspace, row pool and outputs), each running batch or
+ * large request the class-kernel slots it uses while it runs (fewer slots when
+ * the cap leaves less room), and each completed result its size until the
+ * caller collects it (a batch's results share one block, released with the
+ * last of them; uncollected results therefore hold admission back).
  * Admitted requests wait in two queues, batchable orders (visited bitmaps on
  * chip) and large ones; a free slot of `streams` takes whichever holds the
  * oldest request: all waiting batchable requests (up to max_batch) as one
- * multi-matrix batch, or one large request alone, so a large request never
- * holds up the small ones.  Slots launch as soon as they are free, so their
+ * multi-matrix batch, or one large request alone (one at a time: they share
+ * the library's class slots), so a large request never holds up the small
+ * ones.  Slots launch as soon as they are free, so their
  * work overlaps on the GPU (opts.max_ctas can split the GPU between slots
  * instead).  A request whose slots alone would exceed the cap runs alone with
  * as many slots as the cap leaves room for (space-budget mode: fewer sources in

@@ -533,7 +533,8 @@ int check_options(const gsofa_options* in, gsofa_options* o) {
   o->work_chunk = in->work_chunk;
   o->list_capacity = in->list_capacity;
   o->fill_first = in->fill_first ? 1 : 0;
-  o->collect_stats = in->collect_stats ? 1 : 0;
+  if (in->collect_stats < 0 || in->collect_stats > 2) return GSOFA_E_INVAL;
+  o->collect_stats = in->collect_stats;
   o->validate = in->validate;
   if (o->chunk_size > 1024) return GSOFA_E_INVAL;
   return GSOFA_OK;
@@ -675,7 +676,7 @@ int run_device(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
     a.fill_count = out->fill_count;
     a.ctr = ctr;
     a.fill_first = o.fill_first;
-    a.collect_stats = o.collect_stats;
+    a.collect_stats = o.collect_stats == 1;  // work counters (2: times only)
     ev.rec(2, st);
     if (plan.S < n) {
       a.order = order + plan.S;
@@ -1044,7 +1045,7 @@ cudaError_t enqueue_phase1(const BatchPlan& p, const gsofa_options& o, cudaStrea
   a.fill_count = p.fill;
   a.ctr = p.ctr();
   a.fill_first = (o.fill_first || p.shape.fill_first) ? 1 : 0;
-  a.collect_stats = o.collect_stats;
+  a.collect_stats = o.collect_stats == 1;  // work counters (2: times only)
   a.mats = p.d_mats;
   a.item_start = p.d_item_start;
   a.mat_order = p.d_mat_order;
@@ -1789,7 +1790,7 @@ int run_single(Ctx* c, int32_t n, const int32_t* d_rowptr, const int32_t* d_coli
         gsofa_options t = o;
         t.frontier_order = cand == 2 ? 2 : 1;
         t.fill_first = cand == 3 ? 1 : o.fill_first;
-        t.collect_stats = 1;
+        t.collect_stats = 2;  // phase times without the work counters
         t.autotune = 0;
         for (int rep = 0; rep < 2; rep++) {  // the first run also sizes the row pool
           gsofa_result r;

@@ -1,8 +1,10 @@
 // Serving: continuous batching of incoming sparsity patterns.
 //
 // Requests are admitted in arrival order while their projected device memory
-// (CSR copy, per-row workspace, row pool and outputs, class-kernel slots for
-// large orders) fits under the configured cap.  Admitted requests wait in two
+// (CSR copy, per-row workspace, row pool and outputs) fits under the configured
+// cap; the class-kernel slots of a batch or of a large request are charged
+// while that work runs (fewer slots when the cap leaves less room), not while
+// it waits.  Admitted requests wait in two
 // queues: batchable ones (orders whose visited bitmaps fit on chip) and large
 // ones.  Each of `streams` stream slots has a dispatcher thread; a free slot
 // takes whichever queue holds the oldest request: every batchable request
@@ -50,7 +52,9 @@ struct Request {
   const int32_t* h_rp = nullptr;    // host CSR to copy in (on_device == 0)
   const int32_t* h_ci = nullptr;
   int32_t* own = nullptr;           // server copy of a host CSR (rowptr then colidx)
-  int64_t projected = 0;
+  int64_t projected = 0;             // bytes with the class slots of a large request
+  int64_t slot_part = 0;             // of which class slots: charged while the request runs, not while it waits
+  int64_t slot_one = 0;              // bytes of one of those slots
   int64_t est = 0;                  // projected nnz(L+U): the first row-pool size of its batch share
   int64_t budget = 0;               // space-budget mode: mem_budget_bytes of this request (0: server default)
   bool big = false;                 // runs alone (order above the on-chip limit)
@@ -78,6 +82,7 @@ struct gsofa_server {
   std::unordered_map<uint64_t, Request*> live;
   int64_t in_use = 0;
   int32_t inflight = 0;
+  int32_t big_running = 0;                 // large requests on the GPU (at most one)
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
@@ -116,9 +121,10 @@ int64_t projected_bytes(const gsofa_server* S, int32_t n, int64_t nnz, bool host
 void admit(gsofa_server* S) {
   while (!S->pending.empty()) {
     Request* r = S->pending.front();
-    if (S->inflight >= S->cfg.max_inflight || S->in_use + r->projected > S->cfg.mem_cap_bytes) break;
+    const int64_t charge = r->projected - r->slot_part;
+    if (S->inflight >= S->cfg.max_inflight || S->in_use + charge > S->cfg.mem_cap_bytes) break;
     S->pending.pop_front();
-    S->in_use += r->projected;
+    S->in_use += charge;
     if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
     S->inflight++;
     (r->big ? S->ready_big : S->ready_small).push_back(r);
@@ -152,14 +158,21 @@ void worker_loop(gsofa_server* S, int slot) {
     take.clear();
     int64_t reserved = 0;   // class-slot bytes of a batch, charged while it runs
     int32_t batch_slots = 0;
+    int64_t big_budget = 0;  // a large request's memory budget when the cap leaves fewer slots
     bool small = false;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !S->ready_small.empty() || !S->ready_big.empty(); });
+      // one large request at a time: large requests share the library's class
+      // slots, so a second one would only wait for them on this slot's thread
+      auto big_ok = [&] { return !S->ready_big.empty() && S->big_running == 0; };
+      S->cv_work.wait(lk, [&] {
+        return (S->stop && S->ready_small.empty() && S->ready_big.empty()) || !S->ready_small.empty() || big_ok();
+      });
       if (S->ready_small.empty() && S->ready_big.empty() && S->stop) return;
       // the queue with the oldest request goes first
       small = !S->ready_small.empty() &&
-              (S->ready_big.empty() || S->ready_small.front()->t_submit <= S->ready_big.front()->t_submit);
+              (!big_ok() || S->ready_small.front()->t_submit <= S->ready_big.front()->t_submit);
+      if (!small) S->big_running++;
       if (small) {
         int32_t nmax = 0;
         while (!S->ready_small.empty() && (int)take.size() < S->cfg.max_batch) {
@@ -176,8 +189,21 @@ void worker_loop(gsofa_server* S, int slot) {
         S->in_use += reserved;
         if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
       } else {
-        take.push_back(S->ready_big.front());
+        Request* r = S->ready_big.front();
+        take.push_back(r);
         S->ready_big.pop_front();
+        // its class slots, charged while it runs: as many as the cap leaves room for
+        if (r->slot_one > 0 && r->slot_part > 0) {
+          const int64_t room = S->cfg.mem_cap_bytes - S->in_use;
+          int64_t slots = r->slot_part / r->slot_one;
+          if (slots * r->slot_one > room) {
+            slots = std::max<int64_t>(1, room / r->slot_one);
+            big_budget = 2 * slots * r->slot_one;  // the class kernel takes half of mem_budget_bytes
+          }
+          reserved = slots * r->slot_one;
+          S->in_use += reserved;
+          if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
+        }
       }
     }
     // batches on the slot's stream, a large request on its high-priority one
@@ -248,6 +274,7 @@ void worker_loop(gsofa_server* S, int slot) {
       // its time is set by the serial class chains of its largest sources
       gsofa_options o = S->cfg.opts;
       if (take[0]->budget > 0) o.mem_budget_bytes = take[0]->budget;
+      if (big_budget > 0) o.mem_budget_bytes = big_budget;
       if (o.max_ctas == 0) o.max_ctas = S->sms * 4;
       run_alone(0, o);
     }
@@ -268,6 +295,10 @@ void worker_loop(gsofa_server* S, int slot) {
     S->batches++;
     S->launches += launches;
     S->in_use -= reserved;
+    if (!small) {
+      S->big_running--;
+      S->cv_work.notify_all();
+    }
     Charge* ch = nullptr;
     for (int i = 0; i < k; i++) {
       if (rcs[i] != GSOFA_OK) continue;
@@ -292,7 +323,7 @@ void worker_loop(gsofa_server* S, int slot) {
         S->failed++;
       }
       r->done = true;
-      S->in_use -= r->projected;
+      S->in_use -= r->projected - r->slot_part;
       S->inflight--;
     }
     if (ch) {  // the results stay charged until collected
@@ -407,6 +438,10 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
   if (r->nnz < 0) { delete r; return GSOFA_E_INVAL; }
   r->est = projected_entries(n, r->nnz);
   r->projected = projected_bytes(S, n, r->nnz, !on_device);
+  if (n > S->smem_max_n) {
+    r->slot_part = global_tier_bytes(n, &S->cfg.opts);
+    r->slot_one = global_slot_bytes(n);
+  }
   if (r->projected > S->cfg.mem_cap_bytes && n > S->smem_max_n) {
     // space-budget mode (the concurrent-source budget of Section 5, Eq. 1): run
     // the request with as many global-tier slots as the cap leaves room for
@@ -416,6 +451,7 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
     if (slots >= 1) {
       r->budget = 2 * slots * one;  // the global tier takes half of mem_budget_bytes
       r->projected = base + slots * one;
+      r->slot_part = slots * one;
     } else if (S->cfg.opts.host_spill >= 0) {
       // not even one whole slot: the slots' logs in host memory, their
       // visited bitmaps alone on the device (Section 6 external frontier)
@@ -424,6 +460,8 @@ int gsofa_server_submit(gsofa_server* S, int32_t n, const int32_t* rowptr, const
       if (hs >= 1) {
         r->budget = 2 * hs * dev;
         r->projected = base + hs * dev;
+        r->slot_part = hs * dev;
+        r->slot_one = dev;
       }
     }
   }

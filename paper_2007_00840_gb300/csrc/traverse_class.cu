@@ -60,6 +60,7 @@ struct CtCtl {
   int t;          // the class being expanded (-1: no pending class)
   int qcnt[3];    // rotating level lengths
   int smin, smax; // summary words touched (global V)
+  int cmin;       // team mode: the smallest seed below the source
 };
 
 // ---- primitive bit operations
@@ -803,20 +804,25 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
   // seeds: neighbours below s are classes with maxId -1; above s, U entries
   const int rb = __ldg(sc.rowptr + s), re = __ldg(sc.rowptr + s + 1);
   int diag = 0;
+  int wmin = 0x7FFFFFFF;  // the first class: no vertex below it is reached yet
   for (int e = rb + tid; e < re; e += nthr) {
     const int w = __ldg(sc.colidx + e);
     if ((unsigned)w >= (unsigned)sc.n) { cn.bad = 1; continue; }
     if (w == s) { diag = 1; continue; }
+    if (w < s) wmin = min(wmin, w);
     v_set<VM>(tm, w, st);
   }
+  wmin = __reduce_min_sync(FULL, wmin);
   if constexpr (TEAM) {
+    if (lane == 0) atomicMin(&ctl->cmin, wmin);
     diag = __syncthreads_or(diag);
+    wmin = ctl->cmin;
   } else {
     diag = __any_sync(FULL, diag);
     __syncwarp();
   }
 
-  int cursor = 0, nL = 0;
+  int cursor = wmin < s ? wmin : s, nL = 0;
   int skip = 0, fails = 0;  // clean-head gathers (leader only)
   int level = 0;  // team mode: running level index (queues and counters rotate with it)
   for (;;) {
@@ -945,6 +951,7 @@ __global__ void __launch_bounds__(CT_THREADS, MINB) trav_class_kernel(TravArgs a
       if (threadIdx.x == 0) {
         const int k = atomicAdd(&a.ctr->work_team, 1);
         ctl->src = (k < a.ct_nbig && !input_error(a.ctr)) ? k : -1;
+        ctl->cmin = 0x7FFFFFFF;
       }
       __syncthreads();
       const int k = ctl->src;
