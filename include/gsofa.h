@@ -72,8 +72,11 @@ typedef struct gsofa_options {
                                     (n, nnz) (frontier order, and the fill-first check for breadth-first).
                                     0 = heuristic choices */
     int32_t work_chunk;          /* work items a CTA takes per fetch (default 1) */
-    int32_t list_capacity;       /* frontier list entries kept in shared memory (default 2,048, fewer if the
-                                    occupancy needs it; the rest spills to global memory) */
+    int32_t list_capacity;       /* frontier list entries kept in shared memory, the rest spilling to global
+                                    memory: breadth-first kernel, per CTA (default 2,048, fewer if the
+                                    occupancy needs it); class-ordered kernel on one matrix, per warp and
+                                    level parity (default 512 with visited bitmaps in global memory,
+                                    else 128; 32-1024) */
     int32_t max_ctas;            /* cap on traversal CTAs per launch, so concurrent launches share the GPU
                                     (default 0: one full wave) */
     int32_t frontier_order;      /* 0: automatic: class order for every source (sources below an explicit
@@ -121,13 +124,14 @@ typedef struct gsofa_options {
  * vertices_expanded always. */
 typedef struct gsofa_stats {
     float ms_validate, ms_traverse, ms_emit, ms_supernode, ms_total;
-    float ms_traverse_smem, ms_traverse_global;
+    float ms_traverse_smem;      /* breadth-first shared-memory kernel (sources below smem_max_source) */
+    float ms_traverse_global;    /* class-ordered kernel (every other source; all of them by default) */
     int32_t traverse_launches;
     int32_t kernel_launches;     /* every kernel this call launched */
     int64_t vertices_expanded;   /* frontier expansions, revisits included */
     int64_t edges_scanned;       /* adjacency entries read by expansions */
     int64_t pool_retries;        /* times the row pool had to grow and the traversal rerun */
-    int64_t levels;              /* shared-memory tier: frontier levels summed over sources */
+    int64_t levels;              /* frontier levels summed over sources (both kernels) */
     int64_t cycles_traverse;     /* shared-memory tier: SM cycles in frontier levels, summed over sources */
     int64_t cycles_emit;         /* shared-memory tier: SM cycles emitting rows, summed over sources */
 } gsofa_stats;

@@ -261,10 +261,11 @@ int clean_heads_mode(int opt, int vm) {
   return opt == 1 ? 0 : 1;
 }
 
-ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
+ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm, int queue = 0) {
   (void)c;
   ClassCfg k;
   k.warps_per_sm = warps_per_sm;
+  if (queue > 0) k.qw = queue < 32 ? 32 : (queue > 1024 ? 1024 : queue & ~31);
   const int want = warps_per_sm / CLASS_WARPS_PER_CTA;
   const int words = (n_max + 31) / 32;
   const int occ_sv = trav_class_occupancy(CLASS_VM_SMEM, warps_per_sm, words, k.qw);
@@ -279,6 +280,10 @@ ClassCfg class_config(const Ctx* c, int32_t n_max, int warps_per_sm) {
     k.vwords = words;
     const int occ = trav_class_occupancy(CLASS_VM_GLOBAL, warps_per_sm, k.vwords, k.qw);
     k.ctas_per_sm = occ < want ? occ : want;
+    // default queues: 512 entries hold most levels of a large source on chip
+    // (1M ND grid 81 -> 79 ms; 768 and more took the L1 the records need)
+    if (queue <= 0 && trav_class_occupancy(CLASS_VM_GLOBAL, warps_per_sm, k.vwords, 512) >= k.ctas_per_sm)
+      k.qw = 512;
 
   }
   return k;
@@ -294,7 +299,7 @@ int64_t device_slot_bytes(int64_t cap) { return cap / 8 + cap / 256; }
 // allowed by max_ctas.
 int64_t global_slots(const Ctx* c, int32_t n, const gsofa_options& o, bool host_log = false) {
   const int64_t cap = ((int64_t)n + 1023) / 1024 * 1024;
-  const ClassCfg k = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
+  const ClassCfg k = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32, o.list_capacity);
   int64_t slots = o.max_concurrent > 0 ? o.max_concurrent : (int64_t)c->sms * k.ctas_per_sm * CLASS_WARPS_PER_CTA;
   const int64_t fit = global_budget(c, o) / (host_log ? device_slot_bytes(cap) : slot_bytes(cap));
   if (slots > fit) slots = fit;
@@ -485,7 +490,7 @@ int make_plan(Ctx* c, int32_t n, const gsofa_options& o, Plan* p) {
     p->host_log = o.host_spill > 0 || (o.host_spill == 0 && slots < 1);
     if (p->host_log) slots = global_slots(c, n, o, true);
     if (slots < 1) return GSOFA_E_NOMEM;
-    p->cls = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32);
+    p->cls = class_config(c, n, o.warps_per_sm > 0 ? o.warps_per_sm : 32, o.list_capacity);
     p->glob_block = 32 * CLASS_WARPS_PER_CTA;
     p->glob_grid = (int)slots;  // slots (warps); small CTAs spread any slot count over every SM
     int64_t nbig = o.team_sources > 0 ? o.team_sources : 0;

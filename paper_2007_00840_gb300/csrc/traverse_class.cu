@@ -156,12 +156,18 @@ __device__ int scan_smem(const uint32_t* W, int base, int from, int lim, int lan
   if (from >= lim) return -1;
   const int wfirst = (from - base) >> 5;
   const int wend = (lim - base + 31) >> 5;
-  for (int w0 = wfirst; w0 < wend; w0 += 32) {
+  {  // the word holding `from` first (every lane reads it): the next class is usually there
+    const uint32_t m = W[wfirst] & (0xFFFFFFFFu << ((from - base) & 31));
+    if (m) {
+      const int v = base + (wfirst << 5) + __ffs(m) - 1;
+      return v < lim ? v : -1;
+    }
+  }
+  for (int w0 = wfirst + 1; w0 < wend; w0 += 32) {
     const int j = w0 + lane;
     uint32_t m = 0u;
     if (j < wend) {
       m = W[j];
-      if (j == wfirst) m &= 0xFFFFFFFFu << ((from - base) & 31);
       const int hi = lim - base - (j << 5);
       if (hi < 32) m &= (1u << hi) - 1u;
     }
@@ -302,14 +308,14 @@ __device__ int retire_clean(const TravArgs& a, const Src& sc, const Team& tm, in
   if (tj >= 0) {
     int wv[8];
     int nw = 0;
-    bool csr = sc.ell == nullptr && sc.ellw == nullptr;
+    bool csr = (VM != VM_SMEM || sc.ell == nullptr) && sc.ellw == nullptr;
     if (sc.ellw) {
       const int4 r0 = __ldg(sc.ellw + 2 * (size_t)tj), r1 = __ldg(sc.ellw + 2 * (size_t)tj + 1);
       wv[0] = r0.x; wv[1] = r0.y; wv[2] = r0.z; wv[3] = r0.w;
       wv[4] = r1.x; wv[5] = r1.y; wv[6] = r1.z; wv[7] = r1.w;
       if (wv[0] < 0) csr = true;  // sentinel
       else nw = 8;                // empty slots hold t_j itself
-    } else if (!csr) {
+    } else if (VM == VM_SMEM && !csr) {
       const int4 r = __ldg(sc.ell + tj);
       const uint32_t h[4] = {(uint32_t)r.x, (uint32_t)r.y, (uint32_t)r.z, (uint32_t)r.w};
       if ((h[0] & 0xFFFFu) == 0x8000u) {
@@ -468,11 +474,13 @@ __device__ void expand_level(const TravArgs& a, const Src& sc, const Team& tm, C
         }
       }
     } else {
+      // 16-bit records exist only for orders up to 32,768, i.e. with shared
+      // bitmaps; the global-bitmap build reads rows without wide records from the CSR
       uint32_t h[(K + 1) / 2];
 #pragma unroll
       for (int q = 0; q < (K + 1) / 2; q++) h[q] = 0u;
       if (v >= 0) {
-        if (sc.ell) {
+        if (VM == VM_SMEM && sc.ell) {
           if constexpr (K == 8) {
             const int4 r = __ldg(sc.ell + v);
             h[0] = (uint32_t)r.x; h[1] = (uint32_t)r.y; h[2] = (uint32_t)r.z; h[3] = (uint32_t)r.w;
@@ -542,6 +550,43 @@ __device__ void expand_level(const TravArgs& a, const Src& sc, const Team& tm, C
       walk_row<VM, TEAM>(sc, tm, ctl, __shfl_sync(FULL, v, l), t, level, nb, nq, st, bad);
     }
   }
+}
+
+// The head level of class t (one warp): lane q < 8 relaxes slot q of t's
+// record; first-reached vertices below t become the class's level 1, at the
+// start of the odd-level queue (at most 8 entries).  Returns their number, or
+// -1 when t has no record (its row is walked from the CSR by expand).
+template <int VM>
+__device__ __forceinline__ int expand_head(const TravArgs& a, const Src& sc, const Team& tm, int t, VState& st,
+                                           unsigned long long& n_exp, unsigned long long& n_edge) {
+  const int lane = threadIdx.x & 31;
+  int w = t;
+  bool none = sc.ell == nullptr && sc.ellw == nullptr;
+  if (sc.ellw) {
+    if (lane < 8) w = __ldg((const int*)(sc.ellw + 2 * (size_t)t) + lane);
+    none = __shfl_sync(FULL, w, 0) < 0;  // sentinel
+  } else if (sc.ell) {
+    int off = 0;
+    if (lane < 8) off = (int)__ldg((const short*)(sc.ell + t) + lane);
+    none = __shfl_sync(FULL, off, 0) == -32768;  // sentinel
+    w = t + off;                                 // offset 0 (empty slot): w == t
+  }
+  if (none) return -1;
+  if (a.collect_stats && lane == 0) {
+    n_exp++;
+    n_edge += (unsigned long long)(__ldg(sc.rowptr + t + 1) - __ldg(sc.rowptr + t));
+  }
+  const bool pred = lane < 8 && w != t && w != sc.s;
+  const uint32_t bit = 1u << (w & 31);
+  const uint32_t old = v_or_if<VM>(tm, w, pred);
+  bool member = false;
+  if (!(old & bit)) {  // first reach (an OR not issued returns the bit)
+    v_first<VM>(tm, w, old, st);
+    member = w < t;
+  }
+  const unsigned m = __ballot_sync(FULL, member);
+  if (member) tm.qb[__popc(m & ((1u << lane) - 1u))] = w;
+  return __popc(m);
 }
 
 // Lanes per vertex from the level's length: a warp covers 32/LPV vertices per
@@ -869,9 +914,19 @@ __device__ void run_source(const TravArgs& a, const Src& sc, const Team& tm, CtC
       cursor = t + 1;
       if (lane == 0) *l_slot(tm, nL) = t;
       nL++;
-      int qlen = 1;
+      // shared bitmaps: the head level (t alone) by its record's eight lanes,
+      // where most classes end; otherwise (or without a record) the general
+      // level code takes the head too (one call site keeps the kernel small)
+      int qlen = -1;
+      if constexpr (VM == VM_SMEM) {
+        qlen = expand_head<VM>(a, sc, tm, t, st, cn.n_exp, cn.n_edge);
+        if (qlen >= 0) cn.n_lev++;
+        __syncwarp();
+      }
+      const bool head = qlen < 0;
+      if (head) qlen = 1;
       int64_t cb = 0;  // the class's levels overflow into the log from its bottom
-      for (int lv = 0; qlen > 0; lv++) {
+      for (int lv = head ? 0 : 1; qlen > 0; lv++) {
         int nq = 0;
         cn.n_lev++;
         const int64_t nb = lv == 0 ? 0 : next_base(tm, cb, qlen);
